@@ -1,0 +1,258 @@
+/*
+ * lbm.h - C ABI of the GB300 binary Shan-Chen D2Q9 capillary library.
+ *
+ * The library advances the two-component (binary, immiscible) pseudo-
+ * potential lattice Boltzmann model of S. Chibbaro, "Capillary filling with
+ * pseudo-potential binary Lattice-Boltzmann model":
+ *   - per-component BGK equation, Eq. 2 (eq:lbe), Delta t = 1;
+ *   - D2Q9 equilibrium, Eqs. 3-5 with alpha_k = 4/9 and m_k = 1;
+ *   - equilibrium-velocity shift rho_k u_k^eq = rho_k U + tau_k F_k, Eq. 7,
+ *     with the common velocity U of Eq. 8 (sum over the species);
+ *   - bulk force of Eq. 9 with Psi_k = n_k and the coupling written with the
+ *     D2Q9 weights w_i (4/9, 1/9, 1/36): F_k = -G n_k sum_i w_i n_kbar(x+c_i) c_i,
+ *     i.e. G = 9 g of Eq. 10;
+ *   - wall force of Eq. 11 with the same weights:
+ *     F_k^w = -G_kw n_k sum_i w_i s(x+c_i) c_i, s = 1 on solid nodes.
+ *     Positive couplings repel, negative couplings attract (Numerical
+ *     Results section, the two equivalent wetting schemes);
+ *   - geometry of Fig. 1: periodic in x and y; two plates of one solid row
+ *     each span the capillary; half-way bounce-back fused into the pull;
+ *   - interface observables of the Numerical Results section and Figs. 6-8:
+ *     the bulk front where phi = (n_A - n_B)/(n_A + n_B) changes sign on the
+ *     centre row(s), and the precursor film where n_A falls below
+ *     rho_bulk/3 on the fluid rows next to each plate.
+ *
+ * Species A (index 0) is the invading liquid, species B (index 1) the gas.
+ * Lattice units throughout (Delta x = Delta t = 1).
+ *
+ * Conventions for every call:
+ *   - Return value: LBM_OK (0) or a positive LBM_E* code; no exception
+ *     crosses the ABI.  Errors raised by kernels (non-finite mass, timeout)
+ *     are sticky and reported by the next synchronising call.
+ *   - All work is issued on the stream given in lbm_options at creation
+ *     (NULL = the legacy default stream) and is asynchronous unless the
+ *     call says it synchronises.
+ *   - "host" buffers are ordinary CPU memory; "device" buffers are CUDA
+ *     device pointers of the current device.  The caller owns every buffer
+ *     it passes; the library owns the device state behind an lbm_t.
+ *   - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef SHANCHEN_GB300_LBM_H
+#define SHANCHEN_GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBM_OK 0
+#define LBM_EINVAL 1      /* bad argument: tau <= 1/2, non-finite coupling, bad geometry, bad run index */
+#define LBM_ENOMEM 2      /* device allocation failed (library allocator or caller callback) */
+#define LBM_ECUDA 3       /* a CUDA runtime call failed (no device, launch error, ...) */
+#define LBM_ENONFINITE 4  /* a mass sum came out NaN or infinite: the run has diverged */
+#define LBM_ETIMEOUT 5    /* a bounded device wait gave up */
+#define LBM_ESTATE 6      /* the call needs state the handle does not have (no log, t = 0, ...) */
+#define LBM_EIO 7         /* checkpoint file could not be written or read, or is malformed */
+
+/* ---- storage precision of the populations ------------------------------- */
+#define LBM_F64 0   /* FP64 populations and FP64 arithmetic */
+#define LBM_F32 1   /* FP32 populations and FP32 arithmetic */
+#define LBM_F16S 2  /* FP16 storage of f_i - w_i rho_ref,k, FP32 arithmetic */
+
+/* ---- initial layout ------------------------------------------------------ */
+#define LBM_INIT_SLAB 0     /* liquid A on columns [x_lo, x_hi), gas B elsewhere */
+#define LBM_INIT_DROPLET 1  /* liquid A inside the disc |x - (cx, cy)| < r */
+#define LBM_INIT_FIELDS 2   /* caller-given host densities init_nA / init_nB */
+
+typedef struct lbm_s lbm_t;
+
+/* Geometry of one run (Numerical Results section, Fig. 1).
+ * nx, ny      lattice size, x fastest; periodic in x and y; nx, ny >= 1.
+ * cap_x0/x1   the plates cover columns [cap_x0, cap_x1), 0 <= cap_x0 <= cap_x1 <= nx.
+ * y_bot/y_top the two solid plate rows, or -1 for no plate.  The capillary
+ *             height is H = y_top - y_bot - 1 fluid rows.
+ * solid_mask  optional host uint8 [ny][nx]; non-zero = solid.  Replaces the
+ *             plates for the force, the bounce-back and the tracking rows
+ *             (the tracking rows still follow y_bot/y_top).  Copied at create.
+ * init_*      initial layout; the state starts at rest in equilibrium
+ *             (f_i = w_i n_k), solid nodes carry no fluid.  Liquid nodes get
+ *             (n_A, n_B) = (rho_major, rho_minor), gas nodes the reverse.
+ *             init_nA / init_nB (LBM_INIT_FIELDS) are host [ny][nx] arrays,
+ *             copied at create. */
+typedef struct lbm_geometry {
+    int32_t nx, ny;
+    int32_t cap_x0, cap_x1;
+    int32_t y_bot, y_top;
+    int32_t init_kind;
+    int32_t reserved0;
+    const uint8_t* solid_mask;
+    double x_lo, x_hi;
+    double drop_cx, drop_cy, drop_r;
+    double rho_major, rho_minor;
+    const double* init_nA;
+    const double* init_nB;
+} lbm_geometry;
+
+/* Device allocator supplied by the caller (for instance a framework's
+ * caching allocator).  alloc returns NULL on failure. */
+typedef void* (*lbm_alloc_fn)(void* ctx, size_t bytes, void* stream);
+typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
+
+/* Options shared by all runs of a handle.  Fill with lbm_default_options.
+ * precision     LBM_F64 / LBM_F32 / LBM_F16S.
+ * log_every     record (t, z_bulk, z_prec_bottom, z_prec_top, M_A, M_B) every
+ *               log_every steps, including t = 0; 0 = no log.
+ * log_capacity  records kept per run (a ring: the newest log_capacity).
+ * autotune      1 = time the candidate tilings during the first steps of
+ *               lbm_step and keep the fastest.  Tilings change only the
+ *               schedule: results are bit-identical for every tiling.
+ * tile_w        CTA width (64, 128 or 256 threads; 0 = default 128);
+ * tile_h        rows marched per CTA (0 = default 16, clamped to ny).
+ * graph_chunk   steps captured per CUDA graph when the log is off (0 = 64;
+ *               -1 = launch every step directly).
+ * rho_ref       FP16S shift per species (ignored otherwise).
+ * rho_bulk      base of the precursor threshold rho_bulk / 3 (0 = 2.0).
+ * body          constant body acceleration added to both species' a_k
+ *               (drives the Poiseuille check; 0 for capillary filling).
+ * alloc/free    optional device allocator; NULL = cudaMallocAsync on stream.
+ * stream        cudaStream_t of all work; NULL = legacy default stream. */
+typedef struct lbm_options {
+    int32_t precision;
+    int32_t log_every;
+    int32_t log_capacity;
+    int32_t autotune;
+    int32_t tile_w;
+    int32_t tile_h;
+    int32_t graph_chunk;
+    int32_t reserved0;
+    double rho_ref[2];
+    double rho_bulk;
+    double body[2];
+    lbm_alloc_fn alloc;
+    lbm_free_fn free;
+    void* alloc_ctx;
+    void* stream;
+} lbm_options;
+
+/* Description of one run's device storage (for callers that read the raw
+ * populations).  Populations of buffer b live at
+ *   base[b] + ((k * 9 + i) * ny + y) * pitch + x      (elements)
+ * for species k (0 = A, 1 = B), direction i of Eq. 6 in the order
+ * 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ * current is the buffer holding the post-collision populations of time t. */
+typedef struct lbm_run_info {
+    int32_t nx, ny, pitch, precision;
+    int32_t current;
+    int32_t elem_bytes;
+    int64_t time;
+    void* base[2];
+} lbm_run_info;
+
+/* Fills opt with the defaults documented above (FP32, no log, tile 128x16). */
+void lbm_default_options(lbm_options* opt);
+
+/* Creates one run (Model section: Eqs. 2-11 with the given couplings).
+ * G_AB    cross-species coupling G (w_i-weighted, = 9 g of Eq. 10), finite.
+ * wall    {G_Aw, G_Bw}: wall couplings g_kw rho_w of Eq. 11 in w_i units.
+ * tau_A/B relaxation times of Eq. 2, each > 1/2 (nu_k = (tau_k - 1/2)/3).
+ * opt     NULL = defaults.  *out receives the handle (NULL on failure).
+ * Validates every argument before touching the GPU; returns LBM_EINVAL,
+ * LBM_ENOMEM or LBM_ECUDA.  Allocates 2 buffers x 18 populations x ny x pitch
+ * elements plus the log and the reduction scratch; runs the init kernel. */
+int lbm_create(const lbm_geometry* g, double G_AB, const double wall[2], double tau_A,
+               double tau_B, const lbm_options* opt, lbm_t** out);
+
+/* Creates n independent runs advanced together (one launch per step covers
+ * every run).  g, G_AB, tau_A, tau_B have n entries, wall has 2n
+ * ({G_Aw, G_Bw} per run).  Runs never exchange data. */
+int lbm_create_batch(int n, const lbm_geometry* g, const double* G_AB, const double* wall,
+                     const double* tau_A, const double* tau_B, const lbm_options* opt,
+                     lbm_t** out);
+
+/* Advances every run by n_steps >= 0 steps of Eq. 2 (asynchronous).  The
+ * log, when on, is written at every multiple of log_every.  With autotune
+ * on, the first call synchronises while it times the candidate tilings. */
+int lbm_step(lbm_t* h, int64_t n_steps);
+
+/* Blocks until the handle's stream is idle; returns the sticky status. */
+int lbm_sync(lbm_t* h);
+
+/* Time t (steps taken) of the handle.  Host-side counter, no sync. */
+int64_t lbm_time(const lbm_t* h);
+
+/* Number of runs in the handle. */
+int lbm_num_runs(const lbm_t* h);
+
+/* Storage description of run `run` (see lbm_run_info).  No sync. */
+int lbm_run_info_get(const lbm_t* h, int run, lbm_run_info* info);
+
+/* Component densities n_k = sum_i f_i^k at time t (Model section, below
+ * Eq. 6; the collision conserves n_k, so this is the density of the streamed
+ * state of the last step).  nA, nB: [ny][nx] FP64, solid nodes 0.
+ * on_device = 1: device pointers, asynchronous.  on_device = 0: host
+ * pointers, the call synchronises. */
+int lbm_densities(lbm_t* h, int run, double* nA, double* nB, int on_device);
+
+/* Whole-fluid velocity at time t >= 1 (Model section, below Eq. 12):
+ * rho u = sum_k rho_k u_k + (1/2) sum_k F_k with the streamed populations
+ * and the forces of the last step.  ux, uy: [ny][nx] FP64, solid nodes 0.
+ * At t = 0 the fluid is at rest and zeros are written.  on_device as above. */
+int lbm_velocity(lbm_t* h, int run, double* ux, double* uy, int on_device);
+
+/* Front positions at time t, measured from cap_x0 (Numerical Results
+ * section, Figs. 6-8).  z_bulk: phi = 0 crossing on the centre row (odd H)
+ * or the mean over the two centre rows (even H).  z_prec[0], z_prec[1]:
+ * first column from the inlet where n_A < rho_bulk/3 on the fluid row next
+ * to the bottom / top plate.  Each front is linearly interpolated between
+ * the last passing and the first failing column; a row with no failing
+ * column reports the capillary length.  Host outputs; synchronises.
+ * LBM_ESTATE if the run has no capillary (a plate missing). */
+int lbm_interface_positions(lbm_t* h, int run, double* z_bulk, double z_prec[2]);
+
+/* Copies the log ring of run `run` to host rec[capacity][6] (oldest first):
+ * (t, z_bulk, z_prec_bottom, z_prec_top, M_A, M_B).  *n_rec receives the
+ * number of records copied.  Synchronises.  LBM_ESTATE if the log is off. */
+int lbm_get_log(lbm_t* h, int run, double* rec, int capacity, int* n_rec);
+
+/* Per-species mass M_k = sum over fluid nodes and i of f_i^k, summed in
+ * FP64 in a fixed order (deterministic).  The collision and the streaming
+ * with bounce-back conserve it (Numerical Results section: periodic sides
+ * for total mass conservation).  Host output M[2]; synchronises.  Sets and
+ * returns LBM_ENONFINITE if a sum is NaN or infinite. */
+int lbm_mass(lbm_t* h, int run, double M[2]);
+
+/* Copies the populations of time t of run `run` (storage precision, layout
+ * [2][9][ny][nx], FP16S values as stored, i.e. f - w_i rho_ref) into out.
+ * on_device as in lbm_densities. */
+int lbm_populations(lbm_t* h, int run, void* out, int on_device);
+
+/* Tiling in use (CTA width, rows per CTA). */
+int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h);
+
+/* Selects a tiling (tile_w in {64,128,256}, tile_h >= 1).  Results do not
+ * depend on it. */
+int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
+
+/* Writes a checkpoint (header, parameters, populations of time t, log) to
+ * path; lbm_load re-creates the handle so that stepping on gives results
+ * bit-identical to an uninterrupted run.  Both synchronise.  LBM_EIO on
+ * file errors. */
+int lbm_save(lbm_t* h, const char* path);
+int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
+
+/* Sticky device status of the handle (synchronises). */
+int lbm_status(lbm_t* h);
+
+/* Static text for a status code. */
+const char* lbm_error_string(int code);
+
+/* Frees every device allocation of the handle on its stream.  NULL is a no-op. */
+void lbm_destroy(lbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHANCHEN_GB300_LBM_H */

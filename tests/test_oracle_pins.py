@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than its own code: the
+paper's printed formulas in another form (Eq. 6 by trigonometry, Eqs. 3-5 at
+general alpha, Eqs. 9-10 in the paper's g convention), closed forms (moments,
+exact stencil results on linear and quadratic fields, wall-force values),
+invariants (permutation of streaming, mass and momentum conservation) and the
+mechanical equilibrium of a flat interface.  Chosen so that a dropped term, a
+wrong sign, index or weight, or a transposed operand fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _eq6_velocities():
+    """Eq. 6 evaluated with trigonometry."""
+    c = [(0, 0)]
+    for i in range(1, 5):
+        a = (i - 1) * math.pi / 2
+        c.append((round(math.cos(a)), round(math.sin(a))))
+    for i in range(5, 9):
+        a = (i - 5) * math.pi / 2 + math.pi / 4
+        c.append((round(math.sqrt(2) * math.cos(a)), round(math.sqrt(2) * math.sin(a))))
+    return c
+
+
+def _lattice(geom, prm=None, fields=None, seed=0):
+    prm = prm or W.params(1.0, 1.0, 1.0)
+    if fields is None:
+        fields = W.random_fields(geom, seed)
+    return oracle.OracleLattice(geom, prm, *fields)
+
+
+# ---- Eq. 6 and the streaming step of Eq. 2 ------------------------------------
+
+def test_streaming_moves_each_population_along_eq6_velocity():
+    geom = W.periodic_box(7, 6)
+    o = _lattice(geom)
+    c = _eq6_velocities()
+    for i in range(9):
+        F = np.zeros((2, 9, 6, 7))
+        F[0, i, 2, 3] = 1.0
+        F[1, i, 4, 1] = 2.0
+        out = o.stream(F)
+        cx, cy = c[i]
+        assert out[0, i, (2 + cy) % 6, (3 + cx) % 7] == 1.0
+        assert out[1, i, (4 + cy) % 6, (1 + cx) % 7] == 2.0
+        assert np.count_nonzero(out) == 2
+
+
+def test_bounce_back_reflects_into_opposite_direction():
+    # plate row y = 0 under columns [2, 6): a population at (4, 1) heading
+    # into the plate comes back at the same node with the opposite velocity
+    geom = W.capillary_geometry(8, 6, 2, 6, 0, -1)
+    o = _lattice(geom)
+    c = _eq6_velocities()
+    opp = {i: c.index((-c[i][0], -c[i][1])) for i in range(9)}
+    for i in (4, 7, 8):
+        F = np.zeros((2, 9, 6, 8))
+        F[0, i, 1, 4] = 1.0
+        out = o.stream(F)
+        assert out[0, opp[i], 1, 4] == 1.0
+        assert np.count_nonzero(out) == 1
+
+
+def test_streaming_with_bounce_back_is_a_permutation():
+    geom = W.capillary_geometry(19, 11, 3, 15, 1, 8)
+    o = _lattice(geom)
+    fluid = o.solid() == 0
+    rng = np.random.default_rng(7)
+    F = rng.random((2, 9, 11, 19))
+    F[:, :, ~fluid] = 0.0
+    out = o.stream(F)
+    for k in range(2):
+        a = np.sort(F[k][:, fluid].ravel())
+        b = np.sort(out[k][:, fluid].ravel())
+        assert np.array_equal(a, b)
+
+
+# ---- Eqs. 3-5: equilibrium -------------------------------------------------------
+
+def test_equilibrium_moments_closed_form():
+    c = np.array(_eq6_velocities(), dtype=np.float64)
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        n = rng.uniform(0.01, 3.0)
+        u = rng.uniform(-0.2, 0.2, size=2)
+        f = oracle.feq(n, u[0], u[1])
+        assert abs(f.sum() - n) <= 1e-14 * n
+        assert np.allclose(c.T @ f, n * u, rtol=0, atol=1e-15 * max(n, 1))
+        Pi = np.einsum("i,ia,ib->ab", f, c, c)
+        assert np.allclose(Pi, n * (np.outer(u, u) + np.eye(2) / 3.0), rtol=0, atol=2e-15 * max(n, 1))
+
+
+def _paper_feq(alpha, n, u):
+    """Eqs. 3-5 at general alpha, coefficients read from the golden table."""
+    rows = {}
+    with open(os.path.join(GOLD, "feq_coefficients_eq3_5.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            g, den, a, b, d = line.split()
+            rows[g] = (int(den), eval(a), eval(b), eval(d))  # simple fractions
+    c = np.array(_eq6_velocities(), dtype=np.float64)
+    uu = u @ u
+    out = np.zeros(9)
+    for i in range(9):
+        g = "rest" if i == 0 else ("axis" if i <= 4 else "diag")
+        den, a, b, d = rows[g]
+        cu = c[i] @ u
+        base = alpha * n if i == 0 else (1 - alpha) * n / den
+        out[i] = base + a * n * cu + b * n * cu * cu + d * n * uu
+    return out
+
+
+def test_equilibrium_equals_paper_general_alpha_form_at_four_ninths():
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        n = rng.uniform(0.01, 3.0)
+        u = rng.uniform(-0.3, 0.3, size=2)
+        assert np.allclose(oracle.feq(n, *u), _paper_feq(4.0 / 9.0, n, u), rtol=1e-13, atol=1e-15)
+
+
+# ---- Eqs. 9-11: forces -----------------------------------------------------------
+
+def test_bulk_force_on_linear_and_quadratic_fields_is_exact_gradient():
+    # sum_i w_i c_i (c_i . s) = s / 3 and the third moment of w_i vanishes, so
+    # a_A = -G/3 grad n_B exactly for fields of degree <= 2 (away from the wrap)
+    nx, ny = 16, 12
+    geom = W.periodic_box(nx, ny)
+    G = 1.3
+    o = _lattice(geom, W.params(G, 1.0, 1.0))
+    ys, xs = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    nB = 1.0 + 0.01 * xs - 0.02 * ys + 0.001 * xs * ys + 0.0005 * xs ** 2
+    nA = 0.5 + 0.03 * ys + 0.002 * ys ** 2
+    a = o.accel(nA, nB)
+    gBx = 0.01 + 0.001 * ys + 0.001 * xs
+    gBy = -0.02 + 0.001 * xs
+    gAx = np.zeros_like(xs)
+    gAy = 0.03 + 0.004 * ys
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    assert np.allclose(a[0][inner], -G / 3 * gBx[inner], rtol=0, atol=1e-14)
+    assert np.allclose(a[1][inner], -G / 3 * gBy[inner], rtol=0, atol=1e-14)
+    assert np.allclose(a[2][inner], -G / 3 * gAx[inner], rtol=0, atol=1e-14)
+    assert np.allclose(a[3][inner], -G / 3 * gAy[inner], rtol=0, atol=1e-14)
+
+
+def test_bulk_force_equals_paper_eq9_with_g_weights():
+    # Eq. 9 with Eq. 10: F_A = -n_A sum_x' G_AB(x') n_B(x') (x' - x), G = g at
+    # distance 1 and g/4 at sqrt 2, with g = G_w / 9 in the w_i convention
+    nx, ny = 9, 8
+    geom = W.periodic_box(nx, ny)
+    Gw = 1.4
+    g = Gw / 9.0
+    o = _lattice(geom, W.params(Gw, 1.0, 1.0))
+    nA, nB = W.random_fields(geom, 11)
+    a = o.accel(nA, nB)
+    FA = np.zeros((2, ny, nx))
+    FB = np.zeros((2, ny, nx))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dx == 0 and dy == 0:
+                continue
+            gk = g if dx * dx + dy * dy == 1 else g / 4.0
+            nB_s = np.roll(np.roll(nB, -dy, axis=0), -dx, axis=1)   # n_B(x + d)
+            nA_s = np.roll(np.roll(nA, -dy, axis=0), -dx, axis=1)
+            FA[0] -= nA * gk * nB_s * dx
+            FA[1] -= nA * gk * nB_s * dy
+            FB[0] -= nB * gk * nA_s * dx
+            FB[1] -= nB * gk * nA_s * dy
+    assert np.allclose(nA * a[0], FA[0], rtol=1e-12, atol=1e-14)
+    assert np.allclose(nA * a[1], FA[1], rtol=1e-12, atol=1e-14)
+    assert np.allclose(nB * a[2], FB[0], rtol=1e-12, atol=1e-14)
+    assert np.allclose(nB * a[3], FB[1], rtol=1e-12, atol=1e-14)
+
+
+def test_wall_force_closed_form_and_sign():
+    # one plate row at y = 0 under [4, 12) of a 16 x 10 box; Eq. 11 with the
+    # w_i weights gives a^w = -G_kw sum_i w_i s(x + c_i) c_i
+    geom = W.capillary_geometry(16, 10, 4, 12, 0, -1)
+    GAw, GBw = -0.3, 0.25
+    o = _lattice(geom, W.params(0.0, 1.0, 1.0, GAw, GBw))
+    ones = np.ones((10, 16))
+    a = o.accel(ones, ones)
+    # inside the plate span, on the fluid row above it: s at c_4, c_7, c_8
+    # -> sum = (0, -(1/9 + 1/36 + 1/36)) = (0, -1/6)
+    for x in range(5, 11):
+        assert a[0, 1, x] == pytest.approx(0.0, abs=1e-16)
+        assert a[1, 1, x] == pytest.approx(GAw / 6.0, rel=1e-14)
+        assert a[3, 1, x] == pytest.approx(GBw / 6.0, rel=1e-14)
+    # the repulsive coupling pushes B away from the wall (+y), the attractive
+    # one pulls A towards it (-y); the same holds below the plate (row 9)
+    assert a[3, 1, 8] > 0 and a[1, 1, 8] < 0
+    assert a[3, 9, 8] < 0 and a[1, 9, 8] > 0
+    # plate end: (3, 1) sees only (4, 0) through c_8 = (1, -1), weight 1/36
+    assert a[0, 1, 3] == pytest.approx(-GAw / 36.0, rel=1e-14)
+    assert a[1, 1, 3] == pytest.approx(GAw / 36.0, rel=1e-14)
+    # away from the plate there is no wall force
+    assert np.all(a[:, 3:8, :] == 0.0)
+
+
+# ---- invariants of the full step ---------------------------------------------------
+
+def test_mass_conserved_with_plates():
+    geom = W.capillary_geometry(40, 14, 10, 30, 0, 13)
+    o = _lattice(geom, W.params(1.1, 1.0, 0.9, -0.2, 0.1), seed=3)
+    M0 = o.mass()
+    o.step(300)
+    assert np.all(np.abs(o.mass() - M0) <= 1e-13 * M0)
+
+
+def test_total_momentum_conserved_in_periodic_box_with_unequal_tau():
+    # sum_k (n_k U - j_k)/tau_k = 0 by Eq. 8, and the pair forces of Eq. 9
+    # cancel pairwise; a wrong weighting of U or an asymmetric force breaks it
+    geom = W.periodic_box(24, 20)
+    o = _lattice(geom, W.params(1.0, 0.8, 1.3), W.random_fields(geom, 5, 0.2, 1.2))
+    M = o.mass().sum()
+    assert np.all(np.abs(o.momentum()) == 0.0)
+    o.step(150)
+    assert np.all(np.abs(o.momentum()) <= 1e-12 * M)
+
+
+def test_uniform_flow_is_a_fixed_point_and_velocity_has_half_force_term():
+    geom = W.periodic_box(5, 4)
+    u0 = (0.05, -0.03)
+    n0 = (0.9, 0.4)
+    body = (1e-3, 2e-3)
+    o = _lattice(geom, W.params(1.0, 0.9, 1.2, body=body), (np.full((4, 5), n0[0]), np.full((4, 5), n0[1])))
+    F = np.zeros((2, 9, 4, 5))
+    for k in range(2):
+        F[k] = oracle.feq(n0[k], *u0)[:, None, None]
+    o.set_populations(F)
+    o.step(1)
+    ux, uy = o.velocity()
+    # the streamed state is uniform with momentum n u0; the body force adds
+    # half a step of acceleration to the whole-fluid velocity (Model section)
+    assert np.allclose(ux, u0[0] + 0.5 * body[0], rtol=1e-13)
+    assert np.allclose(uy, u0[1] + 0.5 * body[1], rtol=1e-13)
+
+
+# ---- flat interface: mechanical equilibrium with the mixture pressure ------------
+
+def _relax(o, steps, chunk=500):
+    for _ in range(steps // chunk):
+        o.step(chunk)
+    return o
+
+
+def test_flat_interface_mirror_symmetry_and_separation():
+    geom = W.periodic_box(48, 2)
+    o = _lattice(geom, W.params(1.4, 1.0, 1.0), W.slab_fields(geom, 12, 36))
+    _relax(o, 3000)
+    nA, nB = o.densities()
+    # swapping the species and mirroring x about the slab centre is a symmetry
+    mir = (23 - np.arange(48)) % 48
+    assert np.allclose(nA[0], nB[0, mir], rtol=0, atol=1e-11)
+    assert nA[0, 24] > 10 * nB[0, 24]
+
+
+def test_flat_interface_bulk_pressures_equal_mixture_eos():
+    # At a steady flat interface the discrete force telescopes: summed across
+    # the interface, sum_x (F_A + F_B) = -(G/3) [n_A n_B], and the momentum
+    # flux of the steady streamed state balances it.  So the pressure
+    # p = (n_A + n_B)/3 + G n_A n_B/3 (Model section, non-ideal gas law with
+    # c_0^2 = 1/3, written with the w_i-weighted G) is equal in both bulks.
+    # Unequal relaxation times make the two bulks differ, so the equality is
+    # not a symmetry.
+    geom = W.periodic_box(64, 1)
+    G = 1.4
+    o = _lattice(geom, W.params(G, 1.0, 1.3), W.slab_fields(geom, 16, 40))
+    _relax(o, 20000, 2000)
+    a, b = o.densities()
+    pA = oracle.pressure(a[0, 28], b[0, 28], G)
+    pB = oracle.pressure(a[0, 52], b[0, 52], G)
+    assert a[0, 28] > 1.5 and b[0, 52] > 1.5          # separated
+    assert abs(a[0, 28] - b[0, 52]) > 0.1             # the bulks differ
+    assert abs(pA - pB) <= 1e-6 * pA
+
+
+# ---- Laplace's law for a static droplet (Numerical Results section) --------------
+
+@pytest.mark.slow
+def test_laplace_law_droplets():
+    G = 1.4
+    inv_r, dp = [], []
+    for R in (10, 13, 16, 20):
+        geom = W.periodic_box(72, 72)
+        o = _lattice(geom, W.params(G, 1.0, 1.0), W.droplet_fields(geom, 36.0, 36.0, R))
+        o.step(3000)
+        nA, nB = o.densities()
+        p = oracle.pressure(nA, nB, G)
+        # equivalent radius from the amount of A above the outer bulk
+        a_in, a_out = nA[36, 36], nA[0, 0]
+        area = (nA - a_out).sum() / (a_in - a_out)
+        inv_r.append(1.0 / math.sqrt(area / math.pi))
+        dp.append(p[36, 36] - p[0, 0])
+    inv_r, dp = np.array(inv_r), np.array(dp)
+    A = np.vstack([inv_r, np.ones_like(inv_r)]).T
+    (gamma, c0), res, *_ = np.linalg.lstsq(A, dp, rcond=None)
+    r2 = 1 - res[0] / ((dp - dp.mean()) ** 2).sum()
+    assert gamma > 0
+    assert r2 > 0.99
+    assert abs(c0) < 0.1 * gamma * inv_r.min()
+
+
+# ---- single-fluid Poiseuille (Theoretical analysis section) -----------------------
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_poiseuille_profile(tau):
+    # plates at rows 0 and H+1 across the whole width; half-way bounce-back
+    # puts the walls at y = 1/2 and y = H + 1/2; body force g along x:
+    # u(y) = g / (2 nu) (y - 1/2)(H + 1/2 - y), nu = (tau - 1/2)/3
+    H, nx = 16, 4
+    geom = W.capillary_geometry(nx, H + 2, 0, nx, 0, H + 1)
+    g = 1e-6
+    nA = np.ones((H + 2, nx))
+    nA[[0, H + 1], :] = 0.0
+    o = _lattice(geom, W.params(0.0, tau, tau, body=(g, 0.0)), (nA, np.zeros_like(nA)))
+    o.step(12000)
+    ux, uy = o.velocity()
+    y = np.arange(1, H + 1)
+    nu = (tau - 0.5) / 3.0
+    ref = g / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    num = ux[1:H + 1, 0]
+    err = np.sqrt(((num - ref) ** 2).sum() / (ref ** 2).sum())
+    assert err < 0.02
+    assert np.all(np.abs(uy) < 1e-9 * np.abs(ux).max())
+
+
+# ---- interface and precursor fronts (Numerical Results section, Figs. 6-8) --------
+
+def test_front_positions_on_constructed_fields():
+    nx, H = 40, 6
+    geom = W.capillary_geometry(nx, H + 2, 10, 34, 0, H + 1)
+    xs = np.arange(nx, dtype=np.float64)
+    # phi = (nA - nB)/(nA + nB) with nA + nB = 1 and nA = (1 + phi)/2, phi
+    # linear with a zero at x = 21.3 on every row; the wall rows carry a
+    # film whose n_A crosses rho_bulk/3 = 0.6 at x = 27.25 / 25.5
+    phi = np.clip(-(xs - 21.3) / 4.0, -0.9, 0.9)
+    nA = np.repeat(((1 + phi) / 2)[None, :], H + 2, 0)
+    nB = 1.0 - nA
+    film_b = np.clip(1.0 - 0.1 * (xs - 23.25), 0.05, 1.0)
+    film_t = np.clip(1.0 - 0.2 * (xs - 23.5), 0.05, 1.0)
+    nA[1], nA[H] = film_b, film_t
+    nB[1], nB[H] = 0.1, 0.1
+    nA[[0, H + 1], 10:34] = 0.0
+    nB[[0, H + 1], 10:34] = 0.0
+    o = oracle.OracleLattice(geom, dict(W.params(1.0, 1.0, 1.0), rho_bulk=1.8), nA, nB)
+    z = o.interface()
+    assert z[0] == pytest.approx(21.3 - 10, abs=1e-12)
+    assert z[1] == pytest.approx(27.25 - 10, abs=1e-12)
+    assert z[2] == pytest.approx(25.5 - 10, abs=1e-12)
+
+
+def test_front_of_filled_capillary_is_its_length():
+    geom = W.capillary_geometry(30, 8, 5, 25, 0, 7)
+    nA, nB = W.slab_fields(geom, 0, 30)
+    o = oracle.OracleLattice(geom, W.params(1.0, 1.0, 1.0), nA, nB)
+    assert np.all(o.interface() == 20.0)
