@@ -1,0 +1,353 @@
+"""Benchmark of the binary Shan-Chen D2Q9 capillary step on one GB300.
+
+Workload: the single large FP32 capillary, 8192 x 160 lattice, capillary
+length 6144 (plates at rows 0 and 129, H = 128), liquid on x < 2560,
+G = 1.4, tau_A = tau_B = 1, complete-wetting wall coupling; z(t) and the
+FP64 mass sums logged every 50 steps.  A "step" is one lattice time step of
+the whole hot path: the fused pull-stream + collide kernel on every node, and
+on every 50th step the front reduction and the mass sums.
+
+value     GLUPS (lattice node updates of both species per second, all nodes),
+          device time of the timed steps (CUDA events on the library's stream),
+          with L2 flushed between timed steps.
+e2e       the same metric for the whole job through the C ABI with host
+          buffers: initial fields uploaded from pinned host memory, the steps,
+          the log and the final densities copied back, inside the timed region.
+roofline  the step kernel: algorithmic bytes (18 populations read + written
+          per fluid node, storage precision) / its average launch time,
+          against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference: the FP64 oracle on the host cores.
+
+Multi-GPU (torchrun): every rank advances its own replica of the workload
+(independent runs, no data-path collective); the time is the maximum over
+ranks and value counts the nodes of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2-species D2Q9 GLUPS & HBM-peak fraction; FP32/batched vs FP64 at stated error"
+WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 populations, "
+            "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
+BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
+PROFILE = os.path.join(ROOT, "profiles", "k_step_f32_capillary_8192x160.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
+                  for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "lbm_device.h")]
+
+
+def workload(tau_B: float = 1.0):
+    import workloads as W
+    c = W.config_capillary_8192x160(tau_B=tau_B)
+    return c
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or
+    None if the kernel sources changed since the counters were taken."""
+    try:
+        kv = {}
+        with open(PROFILE) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_hash") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(budget_s: float = 15.0):
+    """The FP64 oracle as it stands, single thread, on full 8192x160 steps."""
+    import oracle
+    import workloads as W
+    c = workload()
+    nA, nB = W.initial_fields(c)
+    o = oracle.OracleLattice(c["geom"], c["params"], nA, nB)
+    nodes = c["geom"]["nx"] * c["geom"]["ny"]
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": nodes * steps / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the full 8192x160 grid, one host thread"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on a window of the workload each step."""
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import workloads as W
+    c = workload()
+    g = c["geom"]
+    # columns per step sized so that warm-up + timed steps take about 90 s
+    nA, nB = W.initial_fields(c)
+    probe = oracle.OracleLattice(W.periodic_box(64, g["ny"]), c["params"], nA[:, 1024:1088], nB[:, 1024:1088])
+    t0 = time.perf_counter()
+    probe.step(3)
+    rate = 3 * 64 * g["ny"] / (time.perf_counter() - t0)
+    total = max(1, args.steps + args.warmup)
+    ncols = int(max(8, min(g["nx"], rate * 90.0 / total / g["ny"])))
+    x0 = g["cap_x0"] - ncols // 4
+    sub = dict(nx=ncols, ny=g["ny"], cap_x0=g["cap_x0"] - x0, cap_x1=min(ncols, g["cap_x1"] - x0),
+               y_bot=g["y_bot"], y_top=g["y_top"])
+    sA = np.ascontiguousarray(nA[:, x0:x0 + ncols])
+    sB = np.ascontiguousarray(nB[:, x0:x0 + ncols])
+    o = oracle.OracleLattice(sub, c["params"], sA, sB)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    nodes = ncols * g["ny"]
+    value = nodes * args.steps / dt / 1e9
+    sample = f"{ncols}x{g['ny']} window of the 8192x160 workload at the inlet, FP64 oracle, one host thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(1, args.steps) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(3, args.warmup)
+
+    world, rank, local = dist_setup(args.gpus)
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_0807_0602_gb300.build import build as build_lib
+    from paper_0807_0602_gb300.lbm import Lattice
+
+    if rank == 0:
+        build_lib()
+    barrier(world)
+    build_lib()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    c = workload()
+    g = c["geom"]
+    nodes = g["nx"] * g["ny"]
+    fluid_nodes = nodes - 2 * (g["cap_x1"] - g["cap_x0"])
+    log_every = 50
+    stream = torch.cuda.Stream(device=dev)
+    run = dict(geom=g, params=c["params"], init=c["init"])
+
+    with torch.cuda.stream(stream):
+        lat = Lattice(run, precision=args.precision, log_every=log_every, log_capacity=4096, autotune=True,
+                      stream=stream)
+        lat.step(100)          # autotuning: real steps, every tiling gives the same bits
+        lat.step(args.warmup)
+        lat.sync()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        logged = []
+        t_first = lat.t
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.25)
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+            logged.append((t_first + k + 1) % log_every == 0)
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = sampler.stop()
+        durs = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        total_ms = sum(durs)
+        kern = [d for d, lg in zip(durs, logged) if not lg]
+        kernel_ms = statistics.mean(kern)
+        M = lat.mass()
+        finite = bool(np.all(np.isfinite(M)))
+        tile = lat.tiling
+        lat.close()
+
+    total_ms = max_over_ranks(world, total_ms)
+    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
+    n_logs = sum(logged)
+    gpu_launches = args.steps + 4 * n_logs  # step kernel + (track, mass rows, mass final, log advance)
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    nA0, nB0 = W.initial_fields(c)
+    hA = torch.from_numpy(nA0).pin_memory()
+    hB = torch.from_numpy(nB0).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        lat2 = Lattice(dict(geom=g, params=c["params"], init=("fields", hA.numpy(), hB.numpy())),
+                       precision=args.precision, log_every=log_every, log_capacity=4096, tile=tile, stream=stream)
+        lat2.step(args.steps)
+        log = lat2.log()
+        dA, dB = lat2.densities()
+        lat2.close()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    h2d = 2 * nodes * 8
+    d2h = log.nbytes + dA.nbytes + dB.nbytes
+    e2e = {"value": world * nodes * args.steps / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    alg_bytes = fluid_nodes * BYTES_PER_NODE[args.precision]
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    traffic = read_traffic() if args.precision == "f32" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": "k_step",
+                "alg_bytes_per_launch": alg_bytes, "kernel_ms": kernel_ms}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [g["nx"], g["ny"]], "fluid_nodes": fluid_nodes,
+                   "precision": args.precision, "tile": list(tile), "log_every": log_every,
+                   "l2": "flushed (256 MB write) between timed steps", "state_finite": finite,
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

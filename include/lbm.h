@@ -236,6 +236,16 @@ int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h);
  * depend on it. */
 int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 
+/* Full schedule of the step kernel: tiling plus the kernel variant
+ * (LBM_KERNEL_REGISTER: pulled populations through registers;
+ * LBM_KERNEL_ASYNC: through a depth-stage cp.async ring in shared memory,
+ * depth 3 or 4; not available for LBM_F16S).  Results do not depend on it.
+ * lbm_set_schedule returns LBM_EINVAL for an unsupported combination. */
+#define LBM_KERNEL_REGISTER 0
+#define LBM_KERNEL_ASYNC 1
+int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
+int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
+
 /* Writes a checkpoint (header, parameters, populations of time t, log) to
  * path; lbm_load re-creates the handle so that stepping on gives results
  * bit-identical to an uninterrupted run.  Both synchronise.  LBM_EIO on

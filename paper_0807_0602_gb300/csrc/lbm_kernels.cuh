@@ -1,0 +1,703 @@
+// Kernels of the binary Shan-Chen D2Q9 step (S. Chibbaro, "Capillary filling
+// with pseudo-potential binary Lattice-Boltzmann model", Model section,
+// Eqs. 2-11; Numerical Results section for geometry, bounce-back and fronts).
+//
+// Included by exactly two translation units: kernels_f64.cu (FP64, built with
+// --fmad=false so that every product and sum is rounded separately, in the
+// canonical order below) and kernels_f32.cu (FP32 and FP16-shifted storage).
+//
+// Canonical per-node order (both precisions; FP64 reproduces it bit for bit):
+//   1. pull: ft_i(x) = F_i(x - c_i), or F_opp(i)(x) when x - c_i is solid
+//      (half-way bounce-back fused into the pull)
+//   2. n_k = ((ft_0 + ft_1) + ...) + ft_8; j_k = sum_i c_i ft_i, i ascending
+//   3. S_kbar = sum_{i=1..8} (w_i n_kbar(x + c_i)) c_i, i ascending (Eq. 9 with
+//      the w_i-weighted G, n = 0 on solids); Wl = sum_i (w_i s(x + c_i)) c_i
+//      (Eq. 11); a_k = (-(G S_kbar) - (G_kw Wl)) + g
+//   4. U = (j_A itau_A + j_B itau_B) / (n_A itau_A + n_B itau_B)     (Eq. 8)
+//   5. u_k = U + tau_k a_k                                               (Eq. 7)
+//   6. feq_i = (w_i n_k) (((1 + 3 cu) + 4.5 (cu cu)) - 1.5 usq)   (Eqs. 3-5)
+//   7. F'_i = ft_i - (ft_i - feq_i) itau_k                               (Eq. 2)
+//
+// Step kernel design (sm_103a, HBM-bound stencil, no tensor cores):
+//   - SoA populations, x fastest, rows padded to `pitch`; every load and store
+//     of a warp touches consecutive addresses (the +-1 column shift of the
+//     pull only offsets the warp's 128-byte window by one element).
+//   - A CTA of W threads owns a strip of W - 2 columns (thread t <-> column
+//     x0 - 1 + t; the two edge threads only supply halo densities) and
+//     marches down a segment of rows [y0, y1).  Each row is pulled once: its
+//     18 populations stay in registers for the collision one iteration later,
+//     its two densities go into a 4-row ring in shared memory, so the
+//     8-neighbour force reads densities without an HBM round trip.  One
+//     __syncthreads per row; the ring depth of 4 makes that sufficient.
+//   - Populations are read once and written once per step (72 B/node FP32).
+#pragma once
+
+#include "lbm_device.h"
+
+namespace sc {
+
+template <typename S> struct Prec;
+template <> struct Prec<double> { using C = double; };
+template <> struct Prec<float> { using C = float; };
+template <> struct Prec<__half> { using C = float; };
+
+// D2Q9 weights of Eqs. 3-5 at alpha = 4/9 (correctly rounded divisions).
+template <typename C> struct Wt;
+template <> struct Wt<double> {
+    static constexpr double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+};
+template <> struct Wt<float> {
+    static constexpr float w0 = 4.0f / 9.0f, w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+};
+
+// Storage <-> compute conversion.  FP16S stores f - w_i rho_ref,k.
+__device__ __forceinline__ double dec(double v, double) { return v; }
+__device__ __forceinline__ float dec(float v, float) { return v; }
+__device__ __forceinline__ float dec(__half v, float sh) { return __half2float(v) + sh; }
+__device__ __forceinline__ void enc(double* p, double v, double) { *p = v; }
+__device__ __forceinline__ void enc(float* p, float v, float) { *p = v; }
+__device__ __forceinline__ void enc(__half* p, float v, float sh) { *p = __float2half_rn(v - sh); }
+
+template <typename S> __device__ __forceinline__ S ldg(const S* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __half ldg<__half>(const __half* p) {
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+}
+
+// Shift w_i rho_ref,k of direction group g (0 rest, 1 axis, 2 diagonal).
+template <typename S> struct Shift {
+    using C = typename Prec<S>::C;
+    C v[2][3];
+    __device__ __forceinline__ void load(const RunDesc&) {
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < 3; ++g) v[k][g] = C(0);
+    }
+};
+template <> struct Shift<__half> {
+    float v[2][3];
+    __device__ __forceinline__ void load(const RunDesc& rd) {
+        for (int k = 0; k < 2; ++k) {
+            float r = (float)rd.rho_ref[k];
+            v[k][0] = Wt<float>::w0 * r;
+            v[k][1] = Wt<float>::w1 * r;
+            v[k][2] = Wt<float>::w5 * r;
+        }
+    }
+};
+__device__ __forceinline__ constexpr int grp(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+
+struct Geo {
+    int nx, cx0, cx1, yb, yt;
+    const uint8_t* mask;
+    __device__ __forceinline__ bool solid(int x, int y) const {
+        if (mask) return mask[(long long)y * nx + x] != 0;
+        return (y == yb || y == yt) && x >= cx0 && x < cx1;
+    }
+};
+
+// Solid flags of the 3x3 neighbourhood: bit (dy + 1) * 3 + (dx + 1).
+__device__ __forceinline__ unsigned nbr_solid(const Geo& g, int xm, int xc, int xp, int rm, int rw,
+                                              int rp) {
+    unsigned m = 0;
+    if (g.mask) {
+        const int xs[3] = {xm, xc, xp};
+        const int ys[3] = {rm, rw, rp};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                if (g.mask[(long long)ys[a] * g.nx + xs[b]]) m |= 1u << (a * 3 + b);
+        return m;
+    }
+    const bool r0 = (rm == g.yb || rm == g.yt), r1 = (rw == g.yb || rw == g.yt),
+               r2 = (rp == g.yb || rp == g.yt);
+    if (!(r0 | r1 | r2)) return 0;
+    const bool c0 = xm >= g.cx0 && xm < g.cx1, c1 = xc >= g.cx0 && xc < g.cx1,
+               c2 = xp >= g.cx0 && xp < g.cx1;
+    m |= (unsigned)(r0 && c0) << 0 | (unsigned)(r0 && c1) << 1 | (unsigned)(r0 && c2) << 2;
+    m |= (unsigned)(r1 && c0) << 3 | (unsigned)(r1 && c1) << 4 | (unsigned)(r1 && c2) << 5;
+    m |= (unsigned)(r2 && c0) << 6 | (unsigned)(r2 && c1) << 7 | (unsigned)(r2 && c2) << 8;
+    return m;
+}
+#define SOL(m, dy, dx) (((m) >> (((dy) + 1) * 3 + ((dx) + 1))) & 1u)
+
+// Pull of one node (step 1) and its densities (step 2).
+template <typename S>
+__device__ __forceinline__ void pull_node(const S* __restrict__ src, long long plane, long long own,
+                                          long long oxm, long long oxp, long long orm, long long orp,
+                                          long long orm_xm, long long orm_xp, long long orp_xm,
+                                          long long orp_xp, unsigned sm, const Shift<S>& sh,
+                                          typename Prec<S>::C (&f)[2][9]) {
+    // source of direction i is x - c_i; offsets: own row/col combos
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const S* p = src + (long long)k * 9 * plane;
+        f[k][0] = dec(ldg(p + own), sh.v[k][0]);
+        f[k][1] = dec(ldg(SOL(sm, 0, -1) ? p + 3 * plane + own : p + 1 * plane + oxm), sh.v[k][1]);
+        f[k][2] = dec(ldg(SOL(sm, -1, 0) ? p + 4 * plane + own : p + 2 * plane + orm), sh.v[k][1]);
+        f[k][3] = dec(ldg(SOL(sm, 0, 1) ? p + 1 * plane + own : p + 3 * plane + oxp), sh.v[k][1]);
+        f[k][4] = dec(ldg(SOL(sm, 1, 0) ? p + 2 * plane + own : p + 4 * plane + orp), sh.v[k][1]);
+        f[k][5] = dec(ldg(SOL(sm, -1, -1) ? p + 7 * plane + own : p + 5 * plane + orm_xm), sh.v[k][2]);
+        f[k][6] = dec(ldg(SOL(sm, -1, 1) ? p + 8 * plane + own : p + 6 * plane + orm_xp), sh.v[k][2]);
+        f[k][7] = dec(ldg(SOL(sm, 1, 1) ? p + 5 * plane + own : p + 7 * plane + orp_xp), sh.v[k][2]);
+        f[k][8] = dec(ldg(SOL(sm, 1, -1) ? p + 6 * plane + own : p + 8 * plane + orp_xm), sh.v[k][2]);
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ C dens9(const C (&f)[9]) {
+    return ((((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8]);
+}
+
+struct RowIdx {
+    int rm, rw, rp;
+};
+__device__ __forceinline__ RowIdx rows_of(int r, int ny) {
+    int rw = r % ny;
+    if (rw < 0) rw += ny;
+    RowIdx q;
+    q.rw = rw;
+    q.rm = rw == 0 ? ny - 1 : rw - 1;
+    q.rp = rw == ny - 1 ? 0 : rw + 1;
+    return q;
+}
+
+// Per-CTA constants of the step.
+template <typename S>
+struct StepCtx {
+    using C = typename Prec<S>::C;
+    C G, Gw[2], tau[2], itau[2], gx, gy;
+    Shift<S> sh;
+    __device__ __forceinline__ void load(const RunDesc& rd) {
+        sh.load(rd);
+        G = (C)rd.G;
+        Gw[0] = (C)rd.GwA;
+        Gw[1] = (C)rd.GwB;
+        tau[0] = (C)rd.tauA;
+        tau[1] = (C)rd.tauB;
+        itau[0] = (C)rd.itauA;
+        itau[1] = (C)rd.itauB;
+        gx = (C)rd.gx;
+        gy = (C)rd.gy;
+    }
+};
+
+// Steps 2-7 at one fluid node of row `rw`, column `xc` (thread t of the
+// strip): densities of this and the neighbouring nodes come from the shared
+// ring (slots of rows r-1, r, r+1), the node's pulled populations from fc.
+// MODE 0 writes the post-collision populations, MODE 1 the whole-fluid
+// velocity rho u = sum_k j_k + (1/2) sum_k n_k a_k.
+template <typename S, int W, int MODE>
+__device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+                                             const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
+                                             S* __restrict__ dst, long long plane, long long o, MomOut mo,
+                                             long long mo_idx) {
+    using C = typename Prec<S>::C;
+    using Wc = Wt<C>;
+    C n[2], jx[2], jy[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const C(&f)[9] = fc[k];
+        n[k] = sd[s_0][k][t];
+        jx[k] = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
+        jy[k] = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+    }
+    // wall sum of Eq. 11, the same for both species
+    C Wx = C(0), Wy = C(0);
+    if (m) {
+        if (SOL(m, 0, 1)) Wx = Wx + Wc::w1;                           // i = 1
+        if (SOL(m, 1, 0)) Wy = Wy + Wc::w1;                           // i = 2
+        if (SOL(m, 0, -1)) Wx = Wx - Wc::w1;                          // i = 3
+        if (SOL(m, -1, 0)) Wy = Wy - Wc::w1;                          // i = 4
+        if (SOL(m, 1, 1)) { Wx = Wx + Wc::w5; Wy = Wy + Wc::w5; }     // i = 5
+        if (SOL(m, 1, -1)) { Wx = Wx - Wc::w5; Wy = Wy + Wc::w5; }    // i = 6
+        if (SOL(m, -1, -1)) { Wx = Wx - Wc::w5; Wy = Wy - Wc::w5; }   // i = 7
+        if (SOL(m, -1, 1)) { Wx = Wx + Wc::w5; Wy = Wy - Wc::w5; }    // i = 8
+    }
+    // bulk force of Eq. 9 from the neighbour densities of the other species
+    C ax[2], ay[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int kb = 1 - k;
+        const C n1 = sd[s_0][kb][t + 1], n2 = sd[s_p][kb][t], n3 = sd[s_0][kb][t - 1], n4 = sd[s_m][kb][t],
+                n5 = sd[s_p][kb][t + 1], n6 = sd[s_p][kb][t - 1], n7 = sd[s_m][kb][t - 1], n8 = sd[s_m][kb][t + 1];
+        const C Sx = ((((Wc::w1 * n1 - Wc::w1 * n3) + Wc::w5 * n5) - Wc::w5 * n6) - Wc::w5 * n7) + Wc::w5 * n8;
+        const C Sy = ((((Wc::w1 * n2 - Wc::w1 * n4) + Wc::w5 * n5) + Wc::w5 * n6) - Wc::w5 * n7) - Wc::w5 * n8;
+        ax[k] = (-(cx.G * Sx) - (cx.Gw[k] * Wx)) + cx.gx;
+        ay[k] = (-(cx.G * Sy) - (cx.Gw[k] * Wy)) + cx.gy;
+    }
+    if (MODE == 1) {
+        mo.ux[mo_idx] = (double)(((jx[0] + jx[1]) + C(0.5) * ((n[0] * ax[0]) + (n[1] * ax[1]))) / (n[0] + n[1]));
+        mo.uy[mo_idx] = (double)(((jy[0] + jy[1]) + C(0.5) * ((n[0] * ay[0]) + (n[1] * ay[1]))) / (n[0] + n[1]));
+        return;
+    }
+    // common velocity (Eq. 8) and shifted equilibrium velocities (Eq. 7)
+    const C den = n[0] * cx.itau[0] + n[1] * cx.itau[1];
+    const C Ux = (jx[0] * cx.itau[0] + jx[1] * cx.itau[1]) / den;
+    const C Uy = (jy[0] * cx.itau[0] + jy[1] * cx.itau[1]) / den;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const C ux = Ux + cx.tau[k] * ax[k];
+        const C uy = Uy + cx.tau[k] * ay[k];
+        const C usq = ux * ux + uy * uy;
+        const C b = C(1.5) * usq;
+        const C wn0 = Wc::w0 * n[k], wn1 = Wc::w1 * n[k], wn5 = Wc::w5 * n[k];
+        const C cu[9] = {C(0), ux, uy, -ux, -uy, ux + uy, -ux + uy, -ux - uy, ux - uy};
+        S* d = dst + (long long)k * 9 * plane + o;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
+            const C c = cu[i];
+            const C feq = wn * (((C(1) + C(3) * c) + C(4.5) * (c * c)) - b);   // Eqs. 3-5
+            const C f = fc[k][i];
+            enc(d + (long long)i * plane, f - (f - feq) * cx.itau[k], cx.sh.v[k][grp(i)]);   // Eq. 2
+        }
+    }
+}
+
+// Column bookkeeping of a strip: thread t <-> column x0 - 1 + t (wrapped).
+struct StripCols {
+    int xc, xm, xp, ncols;
+    bool dcol, coll;
+    __device__ __forceinline__ StripCols(int x0, int nx, int W, int t) {
+        ncols = min(W - 2, nx - x0);
+        dcol = t < ncols + 2;
+        coll = t >= 1 && t <= ncols;
+        xc = x0 - 1 + t;
+        if (xc < 0) xc += nx;
+        else if (xc >= nx) xc -= nx;
+        if (!dcol) xc = 0;
+        xm = xc == 0 ? nx - 1 : xc - 1;
+        xp = xc == nx - 1 ? 0 : xc + 1;
+    }
+};
+
+// MODE 0: one time step (read buf[parity], write buf[parity ^ 1]).
+// MODE 1: moments of the step from buf[parity] (whole-fluid velocity), no write.
+// Pulled populations travel through registers (plain loads).
+template <typename S, int W, int MODE>
+__global__ void __launch_bounds__(W) k_step(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
+                                            int parity, MomOut mo) {
+    using C = typename Prec<S>::C;
+    __shared__ C sd[4][2][W];
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const StripCols sc(tl.x0, nx, W, t);
+
+    C fc[2][9], fn[2][9];
+    unsigned smc = 0, smn = 0;
+
+    auto pull_row = [&](int r, C (&f)[2][9], unsigned& smask, int slot) {
+        const RowIdx q = rows_of(r, ny);
+        C nA = C(0), nB = C(0);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const long long bw = (long long)q.rw * pitch, bm = (long long)q.rm * pitch,
+                                bp = (long long)q.rp * pitch;
+                pull_node<S>(src, plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc, bm + sc.xm,
+                             bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, cx.sh, f);
+                nA = dens9(f[0]);
+                nB = dens9(f[1]);
+            }
+        }
+        sd[slot][0][t] = nA;
+        sd[slot][1][t] = nB;
+    };
+
+    const int y0 = tl.y0, y1 = tl.y1;
+    pull_row(y0 - 1, fn, smn, 0);
+    pull_row(y0, fc, smc, 1);
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        pull_row(r + 1, fn, smn, s_p);
+        __syncthreads();
+        if (sc.coll) {
+            const RowIdx q = rows_of(r, ny);
+            if (!SOL(smc, 0, 0))
+                collide_node<S, W, MODE>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane,
+                                         (long long)q.rw * pitch + sc.xc, mo, (long long)q.rw * mo.nx + sc.xc);
+            else if (MODE == 1) {
+                mo.ux[(long long)q.rw * mo.nx + sc.xc] = 0.0;
+                mo.uy[(long long)q.rw * mo.nx + sc.xc] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
+        smc = smn;
+    }
+}
+
+// ---- asynchronous-copy variant ---------------------------------------------
+// Same arithmetic and the same strip/row march as k_step, but each thread's
+// 18 pulled values of a row are fetched with cp.async into a D-deep ring of
+// shared-memory stages, D - 1 rows ahead of the row being consumed.  The
+// loads in flight then live in shared memory instead of registers, so every
+// CTA keeps several rows of HBM reads outstanding.  Each thread reads back
+// only the values it copied itself, so the stage ring needs no barrier; only
+// the density ring does (one __syncthreads per row, as in k_step).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes_is_8) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes_is_8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename S, int W, int D>
+__global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
+                                                  int parity) {
+    static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
+    using C = typename Prec<S>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* stage = reinterpret_cast<S*>(smem_raw);                        // [D][18][W]
+    C(*sd)[2][W] = reinterpret_cast<C(*)[2][W]>(smem_raw + (size_t)D * 18 * W * sizeof(S));   // [4][2][W]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const StripCols sc(tl.x0, nx, W, t);
+    const int y0 = tl.y0, y1 = tl.y1;
+
+    // issue the pulls of row p into stage slot p % D; returns nothing, the
+    // solid mask of row p is recomputed when the row is consumed
+    auto issue = [&](int p) {
+        if (p <= y1 && sc.dcol) {
+            const RowIdx q = rows_of(p, ny);
+            const unsigned m = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(m, 0, 0)) {
+                const long long bw = (long long)q.rw * pitch, bm = (long long)q.rm * pitch,
+                                bp = (long long)q.rp * pitch;
+                const long long own = bw + sc.xc;
+                S* st = stage + (size_t)(((p - y0 + 1) % D) * 18) * W + t;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const S* pk = src + (long long)k * 9 * plane;
+                    S* sk = st + k * 9 * W;
+                    const int b8 = sizeof(S) == 8;
+                    cp_async(sk + 0 * W, pk + own, b8);
+                    cp_async(sk + 1 * W, SOL(m, 0, -1) ? pk + 3 * plane + own : pk + 1 * plane + bw + sc.xm, b8);
+                    cp_async(sk + 2 * W, SOL(m, -1, 0) ? pk + 4 * plane + own : pk + 2 * plane + bm + sc.xc, b8);
+                    cp_async(sk + 3 * W, SOL(m, 0, 1) ? pk + 1 * plane + own : pk + 3 * plane + bw + sc.xp, b8);
+                    cp_async(sk + 4 * W, SOL(m, 1, 0) ? pk + 2 * plane + own : pk + 4 * plane + bp + sc.xc, b8);
+                    cp_async(sk + 5 * W, SOL(m, -1, -1) ? pk + 7 * plane + own : pk + 5 * plane + bm + sc.xm, b8);
+                    cp_async(sk + 6 * W, SOL(m, -1, 1) ? pk + 8 * plane + own : pk + 6 * plane + bm + sc.xp, b8);
+                    cp_async(sk + 7 * W, SOL(m, 1, 1) ? pk + 5 * plane + own : pk + 7 * plane + bp + sc.xp, b8);
+                    cp_async(sk + 8 * W, SOL(m, 1, -1) ? pk + 6 * plane + own : pk + 8 * plane + bp + sc.xm, b8);
+                }
+            }
+        }
+        cp_commit();
+    };
+    // consume row p: copy this thread's staged values out, densities to the ring
+    auto consume = [&](int p, C (&f)[2][9], unsigned& smask, int slot) {
+        const RowIdx q = rows_of(p, ny);
+        C nA = C(0), nB = C(0);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const S* st = stage + (size_t)(((p - y0 + 1) % D) * 18) * W + t;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[k][i] = dec(st[(k * 9 + i) * W], cx.sh.v[k][grp(i)]);
+                nA = dens9(f[0]);
+                nB = dens9(f[1]);
+            }
+        }
+        sd[slot][0][t] = nA;
+        sd[slot][1][t] = nB;
+    };
+
+    C fc[2][9], fn[2][9];
+    unsigned smc = 0, smn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) issue(y0 - 1 + j);
+    cp_wait<D - 1>();
+    consume(y0 - 1, fn, smn, 0);
+    issue(y0 - 1 + D);
+    cp_wait<D - 1>();
+    consume(y0, fc, smc, 1);
+    issue(y0 + D);
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        cp_wait<D - 1>();
+        consume(r + 1, fn, smn, s_p);
+        issue(r + 1 + D);
+        __syncthreads();
+        if (sc.coll && !SOL(smc, 0, 0)) {
+            const RowIdx q = rows_of(r, ny);
+            collide_node<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (long long)q.rw * pitch + sc.xc,
+                                  MomOut{nullptr, nullptr, 0}, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
+        smc = smn;
+    }
+    cp_wait<0>();
+}
+
+template <typename S, int W, int D>
+constexpr size_t async_smem_bytes() {
+    return (size_t)D * 18 * W * sizeof(S) + 4 * 2 * W * sizeof(typename Prec<S>::C);
+}
+
+// ---- initial state: f_i = f_i^eq(n^0, u = 0) = w_i n^0 on fluid nodes -----
+template <typename S>
+__global__ void k_init(const RunDesc* __restrict__ runs) {
+    using C = typename Prec<S>::C;
+    using Wc = Wt<C>;
+    const RunDesc& rd = runs[blockIdx.y];
+    Shift<S> sh;
+    sh.load(rd);
+    const Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rd.nodes; q += gridDim.x * blockDim.x) {
+        const int y = q / rd.nx, x = q - y * rd.nx;
+        const bool sol = geo.solid(x, y);
+        double n0[2] = {0.0, 0.0};
+        if (!sol) {
+            bool liquid;
+            if (rd.init_kind == 0) {
+                liquid = (double)x >= rd.x_lo && (double)x < rd.x_hi;
+            } else if (rd.init_kind == 1) {
+                const double dx = __dsub_rn((double)x, rd.cx), dy = __dsub_rn((double)y, rd.cy);
+                liquid = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(rd.r, rd.r);
+            } else {
+                liquid = false;
+            }
+            if (rd.init_kind == 2) {
+                n0[0] = rd.init_nA[q];
+                n0[1] = rd.init_nB[q];
+            } else {
+                n0[0] = liquid ? rd.rho_major : rd.rho_minor;
+                n0[1] = liquid ? rd.rho_minor : rd.rho_major;
+            }
+        }
+        const long long o = (long long)y * rd.pitch + x;
+        for (int b = 0; b < 2; ++b) {
+            S* base = static_cast<S*>(rd.buf[b]);
+            for (int k = 0; k < 2; ++k) {
+                const C n = (C)n0[k];
+                for (int i = 0; i < 9; ++i) {
+                    const C w = i == 0 ? Wc::w0 : (i <= 4 ? Wc::w1 : Wc::w5);
+                    S* p = base + ((long long)k * 9 + i) * rd.plane + o;
+                    if (sol) *p = S(0.0f);
+                    else enc(p, w * n, sh.v[k][grp(i)]);
+                }
+            }
+        }
+    }
+}
+
+// FP64 density of species k at node (x, y): sum of the decoded populations
+// in i order, accumulated in FP64.
+template <typename S>
+__device__ __forceinline__ double node_density(const RunDesc& rd, const S* base, const Shift<S>& sh, int k,
+                                               long long o) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        acc = __dadd_rn(acc, (double)dec(ldg(base + ((long long)k * 9 + i) * rd.plane + o), sh.v[k][grp(i)]));
+    return acc;
+}
+
+template <typename S>
+__global__ void k_densities(const RunDesc* __restrict__ runs, int run, int parity, double* __restrict__ nA,
+                            double* __restrict__ nB) {
+    const RunDesc& rd = runs[run];
+    Shift<S> sh;
+    sh.load(rd);
+    const Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* base = static_cast<const S*>(rd.buf[parity]);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < rd.nodes; q += gridDim.x * blockDim.x) {
+        const int y = q / rd.nx, x = q - y * rd.nx;
+        if (geo.solid(x, y)) {
+            nA[q] = 0.0;
+            nB[q] = 0.0;
+            continue;
+        }
+        const long long o = (long long)y * rd.pitch + x;
+        nA[q] = node_density<S>(rd, base, sh, 0, o);
+        nB[q] = node_density<S>(rd, base, sh, 1, o);
+    }
+}
+
+template <typename S>
+__global__ void k_export(const RunDesc* __restrict__ runs, int run, int parity, S* __restrict__ out) {
+    const RunDesc& rd = runs[run];
+    const S* base = static_cast<const S*>(rd.buf[parity]);
+    const long long total = 18LL * rd.nodes;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long ki = q / rd.nodes;
+        const int rem = (int)(q - ki * rd.nodes);
+        const int y = rem / rd.nx, x = rem - y * rd.nx;
+        out[q] = base[ki * rd.plane + (long long)y * rd.pitch + x];
+    }
+}
+
+template <typename S>
+__global__ void k_import(const RunDesc* __restrict__ runs, int run, int parity, const S* __restrict__ in) {
+    const RunDesc& rd = runs[run];
+    S* base = static_cast<S*>(rd.buf[parity]);
+    const long long total = 18LL * rd.nodes;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long ki = q / rd.nodes;
+        const int rem = (int)(q - ki * rd.nodes);
+        const int y = rem / rd.nx, x = rem - y * rd.nx;
+        base[ki * rd.plane + (long long)y * rd.pitch + x] = in[q];
+    }
+}
+
+// ---- fronts (Numerical Results section, Figs. 6-8) -------------------------
+// One CTA of 4 warps per run; warp w scans tracked row w from cap_x0:
+//   w = 0, 1: the centre row(s) with v = phi = (n_A - n_B)/(n_A + n_B);
+//   w = 2, 3: the fluid rows next to the bottom / top plate with
+//             v = n_A - rho_bulk / 3.
+// The first failing column x* (v < 0) comes from a warp ballot per 32-column
+// chunk; z = (x* - 1 - cap_x0) + v(x* - 1) / (v(x* - 1) - v(x*)), in FP64.
+template <typename S>
+__device__ __forceinline__ double front_value(const RunDesc& rd, const S* base, const Shift<S>& sh, int x,
+                                              int y, bool prec) {
+    const long long o = (long long)y * rd.pitch + x;
+    const double a = node_density<S>(rd, base, sh, 0, o);
+    if (prec) return __dsub_rn(a, rd.thr);
+    const double b = node_density<S>(rd, base, sh, 1, o);
+    return __ddiv_rn(__dsub_rn(a, b), __dadd_rn(a, b));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) k_track(const RunDesc* __restrict__ runs, int parity, LogCtl lc,
+                                               double* __restrict__ zout) {
+    const RunDesc& rd = runs[blockIdx.x];
+    __shared__ double zr[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool has = rd.y_bot >= 0 && rd.y_top >= 0 && rd.y_top - rd.y_bot >= 2 && rd.cap_x1 > rd.cap_x0;
+    if (has) {
+        Shift<S> sh;
+        sh.load(rd);
+        const S* base = static_cast<const S*>(rd.buf[parity]);
+        const int H = rd.y_top - rd.y_bot - 1;
+        int y;
+        if (warp == 0) y = (H % 2 == 0) ? rd.y_bot + H / 2 : rd.y_bot + (H + 1) / 2;
+        else if (warp == 1) y = (H % 2 == 0) ? rd.y_bot + H / 2 + 1 : rd.y_bot + (H + 1) / 2;
+        else if (warp == 2) y = rd.y_bot + 1;
+        else y = rd.y_top - 1;
+        const bool prec = warp >= 2;
+        int found = -1;
+        for (int x0 = rd.cap_x0; x0 < rd.cap_x1 && found < 0; x0 += 32) {
+            const int x = x0 + lane;
+            bool fail = false;
+            if (x < rd.cap_x1) fail = front_value<S>(rd, base, sh, x, y, prec) < 0.0;
+            const unsigned b = __ballot_sync(0xffffffffu, fail);
+            if (b) found = x0 + __ffs(b) - 1;
+        }
+        if (lane == 0) {
+            double z;
+            if (found < 0) {
+                z = (double)(rd.cap_x1 - rd.cap_x0);
+            } else {
+                const int xp = found == 0 ? rd.nx - 1 : found - 1;
+                const double v = front_value<S>(rd, base, sh, found, y, prec);
+                const double vp = front_value<S>(rd, base, sh, xp, y, prec);
+                if (!(vp >= 0.0)) z = (double)(found - rd.cap_x0);
+                else z = __dadd_rn((double)(found - 1 - rd.cap_x0), __ddiv_rn(vp, __dsub_rn(vp, v)));
+            }
+            zr[warp] = z;
+        }
+    } else if (lane == 0) {
+        zr[warp] = __longlong_as_double(0x7ff8000000000000LL);  // NaN: no channel
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double zb;
+        if (has) {
+            const int H = rd.y_top - rd.y_bot - 1;
+            zb = (H % 2 == 0) ? __dmul_rn(0.5, __dadd_rn(zr[0], zr[1])) : zr[0];
+        } else {
+            zb = zr[0];
+        }
+        if (zout) {
+            zout[blockIdx.x * 3 + 0] = zb;
+            zout[blockIdx.x * 3 + 1] = zr[2];
+            zout[blockIdx.x * 3 + 2] = zr[3];
+        }
+        if (rd.log && lc.count) {
+            const long long c = *lc.count;
+            double* rec = rd.log + (c % lc.cap) * 6;
+            rec[0] = (double)(c * (long long)lc.log_every);
+            rec[1] = zb;
+            rec[2] = zr[2];
+            rec[3] = zr[3];
+        }
+    }
+}
+
+// ---- deterministic FP64 mass sums -----------------------------------------
+// Pass 1: one CTA per (run, row): thread t sums columns t, t + 256, ... in
+// order, then a fixed shared-memory tree.  Pass 2: one CTA per run sums its
+// rows the same way.  The order never depends on timing, so repeated runs
+// give identical bits.
+template <typename S>
+__global__ void __launch_bounds__(256) k_mass_rows(const RunDesc* __restrict__ runs, const int2* __restrict__ rows,
+                                                   int parity, double* __restrict__ partials) {
+    const int2 ry = rows[blockIdx.x];
+    const RunDesc& rd = runs[ry.x];
+    Shift<S> sh;
+    sh.load(rd);
+    const Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* base = static_cast<const S*>(rd.buf[parity]);
+    double a = 0.0, b = 0.0;
+    for (int x = threadIdx.x; x < rd.nx; x += 256) {
+        if (geo.solid(x, ry.y)) continue;
+        const long long o = (long long)ry.y * rd.pitch + x;
+        a = __dadd_rn(a, node_density<S>(rd, base, sh, 0, o));
+        b = __dadd_rn(b, node_density<S>(rd, base, sh, 1, o));
+    }
+    __shared__ double s[2][256];
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
+            s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x + 0] = s[0][0];
+        partials[2 * blockIdx.x + 1] = s[1][0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mass_final(const RunDesc* __restrict__ runs,
+                                                    const double* __restrict__ partials, double* __restrict__ mass,
+                                                    LogCtl lc, int write_log, uint32_t* __restrict__ err);
+
+}  // namespace sc

@@ -1,0 +1,127 @@
+// Launchers of the kernels in lbm_kernels.cuh; instantiated per storage type
+// by kernels_f64.cu and kernels_f32.cu.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace sc {
+
+static inline int clamp_grid(long long want, int cap) {
+    if (want < 1) return 1;
+    return want > cap ? cap : (int)want;
+}
+
+template <typename S>
+cudaError_t Launch<S>::init(const RunDesc* d_runs, int nruns, int max_nodes, cudaStream_t s) {
+    if (nruns <= 0) return cudaSuccess;
+    dim3 grid(clamp_grid((max_nodes + 255) / 256, 2048), nruns);
+    k_init<S><<<grid, 256, 0, s>>>(d_runs);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                            cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    MomOut none{nullptr, nullptr, 0};
+    switch (W) {
+        case 64: k_step<S, 64, 0><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 128: k_step<S, 128, 0><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 256: k_step<S, 256, 0><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S, int W, int D>
+static cudaError_t launch_async(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, cudaStream_t s) {
+    constexpr size_t smem = async_smem_bytes<S, W, D>();
+    static bool configured = false;   // attribute set once per process and instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_async<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_async<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if constexpr (sizeof(S) == 2) {
+        return cudaErrorInvalidValue;   // cp.async moves 4 or 8 bytes: FP16 storage uses k_step
+    } else {
+        const int key = W * 10 + D;
+        switch (key) {
+            case 643: return launch_async<S, 64, 3>(d_runs, d_tiles, ntiles, parity, s);
+            case 644: return launch_async<S, 64, 4>(d_runs, d_tiles, ntiles, parity, s);
+            case 1283: return launch_async<S, 128, 3>(d_runs, d_tiles, ntiles, parity, s);
+            case 1284: return launch_async<S, 128, 4>(d_runs, d_tiles, ntiles, parity, s);
+            case 2563: return launch_async<S, 256, 3>(d_runs, d_tiles, ntiles, parity, s);
+            case 2564: return launch_async<S, 256, 4>(d_runs, d_tiles, ntiles, parity, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+template <typename S>
+cudaError_t Launch<S>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                               MomOut out, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step<S, 64, 1><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        case 128: k_step<S, 128, 1><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        case 256: k_step<S, 256, 1><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA, double* nB,
+                                 cudaStream_t s) {
+    k_densities<S><<<clamp_grid((nodes + 255) / 256, 4096), 256, 0, s>>>(d_runs, run, parity, nA, nB);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::track(const RunDesc* d_runs, int nruns, int parity, LogCtl lc, double* zout,
+                             cudaStream_t s) {
+    if (nruns <= 0) return cudaSuccess;
+    k_track<S><<<nruns, 128, 0, s>>>(d_runs, parity, lc, zout);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::mass(const RunDesc* d_runs, int nruns, const int2* d_rows, int nrows, int parity,
+                            double* d_partials, double* d_mass, LogCtl lc, int write_log, uint32_t* d_err,
+                            cudaStream_t s) {
+    if (nruns <= 0) return cudaSuccess;
+    k_mass_rows<S><<<nrows, 256, 0, s>>>(d_runs, d_rows, parity, d_partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<nruns, 256, 0, s>>>(d_runs, d_partials, d_mass, lc, write_log, d_err);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::export_pops(const RunDesc* d_runs, int run, int parity, int nx, int ny, void* out,
+                                   cudaStream_t s) {
+    const long long total = 18LL * nx * ny;
+    k_export<S><<<clamp_grid((total + 255) / 256, 8192), 256, 0, s>>>(d_runs, run, parity, static_cast<S*>(out));
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::import_pops(const RunDesc* d_runs, int run, int parity, int nx, int ny, const void* in,
+                                   cudaStream_t s) {
+    const long long total = 18LL * nx * ny;
+    k_import<S><<<clamp_grid((total + 255) / 256, 8192), 256, 0, s>>>(d_runs, run, parity,
+                                                                      static_cast<const S*>(in));
+    return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -1,0 +1,125 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares.
+
+No compute call runs here: argument validation happens before the library
+touches a GPU, so rejected arguments can be checked on a machine without one.
+"""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    pat = re.compile(r"^\s*(?!typedef)(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*([a-z][a-z0-9_]*)\s*\(")
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        with open(hdr) as fh:
+            for line in fh:
+                m = pat.match(line)
+                if m:
+                    names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0807_0602_gb300 import build as B
+    from paper_0807_0602_gb300 import _lib
+    B.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_step", "lbm_densities", "lbm_interface_positions", "lbm_create_batch",
+                     "lbm_mass", "lbm_get_log", "lbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_every_lbm_symbol():
+    from paper_0807_0602_gb300 import _lib
+    lbm_names = [n for n in declared_functions() if n.startswith("lbm_")]
+    assert set(lbm_names) <= set(_lib.SIGNATURES)
+
+
+def _geom(nx=16, ny=8):
+    from paper_0807_0602_gb300 import _lib as L
+    g = L.Geometry()
+    g.nx, g.ny = nx, ny
+    g.cap_x0, g.cap_x1, g.y_bot, g.y_top = 4, 12, 0, 7
+    g.init_kind = L.LBM_INIT_SLAB
+    g.x_lo, g.x_hi = 0.0, 6.0
+    g.rho_major, g.rho_minor = 2.0, 0.04
+    return g
+
+
+def _create(lib, g, G=1.0, wall=(0.0, 0.0), tA=1.0, tB=1.0, opt=None):
+    h = ctypes.c_void_p()
+    w = (ctypes.c_double * 2)(*wall)
+    rc = lib.lbm_create(ctypes.byref(g), G, w, tA, tB, ctypes.byref(opt) if opt is not None else None,
+                        ctypes.byref(h))
+    return rc, h
+
+
+def test_invalid_arguments_are_rejected_without_touching_the_gpu(lib):
+    from paper_0807_0602_gb300 import _lib as L
+    assert _create(lib, _geom(), tA=0.5)[0] == L.LBM_EINVAL          # tau must exceed 1/2
+    assert _create(lib, _geom(), tB=0.3)[0] == L.LBM_EINVAL
+    assert _create(lib, _geom(), G=math.nan)[0] == L.LBM_EINVAL
+    assert _create(lib, _geom(), wall=(math.inf, 0.0))[0] == L.LBM_EINVAL
+    assert _create(lib, _geom(nx=0))[0] == L.LBM_EINVAL
+    g = _geom()
+    g.cap_x1 = 17                                                    # plates past the grid
+    assert _create(lib, g)[0] == L.LBM_EINVAL
+    g = _geom()
+    g.y_top = 8
+    assert _create(lib, g)[0] == L.LBM_EINVAL
+    g = _geom()
+    g.init_kind = L.LBM_INIT_FIELDS                                  # fields missing
+    assert _create(lib, g)[0] == L.LBM_EINVAL
+    opt = L.Options()
+    lib.lbm_default_options(ctypes.byref(opt))
+    opt.precision = 7
+    assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
+    opt.precision = L.LBM_F32
+    opt.tile_w = 100
+    assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
+    opt.tile_w = 128
+    opt.log_every, opt.log_capacity = 10, 0
+    assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
+
+
+def test_null_handles_and_status_strings(lib):
+    from paper_0807_0602_gb300 import _lib as L
+    assert lib.lbm_step(None, 1) == L.LBM_EINVAL
+    assert lib.lbm_time(None) == -1
+    lib.lbm_destroy(None)
+    for code in range(8):
+        assert lib.lbm_error_string(code)
+    assert lib.lbm_error_string(99) == b"unknown status"
+
+
+def test_default_options(lib):
+    from paper_0807_0602_gb300 import _lib as L
+    opt = L.Options()
+    lib.lbm_default_options(ctypes.byref(opt))
+    assert opt.precision == L.LBM_F32 and opt.tile_w == 128 and opt.tile_h == 16 and opt.rho_bulk == 2.0
+
+
+def test_structure_layouts_match_header():
+    from paper_0807_0602_gb300 import _lib as L
+    # 8 int32 + pointer + 7 doubles + 2 pointers
+    assert ctypes.sizeof(L.Geometry) == 8 * 4 + 8 + 7 * 8 + 2 * 8
+    # 8 int32 + 5 doubles + 4 pointers
+    assert ctypes.sizeof(L.Options) == 8 * 4 + 5 * 8 + 4 * 8
+    assert ctypes.sizeof(L.RunInfo) == 6 * 4 + 8 + 2 * 8

@@ -1,0 +1,274 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 kernels are built without multiply-add contraction and follow the same
+canonical order as the oracle, so they must agree to 1e-12 relative (in
+practice bit for bit).  FP32 and FP16-shifted storage are compared with the
+tolerances stated in each test.  Schedules (tilings, CUDA graphs, batching)
+must not change a single bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_0807_0602_gb300 import build as B
+    B.build()
+    oracle.build()
+
+
+def Lattice(*a, **k):
+    from paper_0807_0602_gb300.lbm import Lattice as _L
+    return _L(*a, **k)
+
+
+def rel_err(a, b, fluid):
+    a, b = a[fluid], b[fluid]
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+CASES = {
+    "box16x8": (W.periodic_box(16, 8), W.params(1.0, 0.8, 1.3), "random"),
+    "capillary64x18": (W.capillary_geometry(64, 18, 16, 48, 0, 17), W.params(1.2, 1.0, 0.9, -0.1, 0.05), "slab"),
+    "odd17x9": (W.capillary_geometry(17, 9, 3, 14, 1, 7), W.params(1.1, 1.2, 0.8, 0.1, -0.1), "random"),
+    "tiny5x4": (W.capillary_geometry(5, 4, 1, 4, 0, 3), W.params(0.9, 1.0, 1.0, -0.2, 0.0), "random"),
+    "row3x1": (W.periodic_box(3, 1), W.params(0.8, 1.0, 0.7), "random"),
+    "wide300x5": (W.capillary_geometry(300, 5, 0, 300, 0, 4), W.params(1.0, 1.0, 1.0, -0.1, 0.1), "random"),
+}
+
+
+def _fields(geom, kind, seed=0):
+    if kind == "random":
+        return W.random_fields(geom, seed, 0.2, 1.2)
+    return W.slab_fields(geom, 0, geom["nx"] // 3)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("steps", [1, 10, 100])
+def test_fp64_matches_oracle(name, steps):
+    geom, prm, kind = CASES[name]
+    nA, nB = _fields(geom, kind)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(steps)
+    fluid = ref.solid() == 0
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64") as lat:
+        lat.step(steps)
+        F = lat.populations()
+        gA, gB = lat.densities()
+        ux, uy = lat.velocity()
+        M = lat.mass()
+    Fr = ref.populations()
+    assert np.max(np.abs(F - Fr)[:, :, fluid] / np.maximum(np.abs(Fr[:, :, fluid]), 1e-300)) <= 1e-12
+    rA, rB = ref.densities()
+    assert rel_err(gA, rA, fluid) <= 1e-12 and rel_err(gB, rB, fluid) <= 1e-12
+    vx, vy = ref.velocity()
+    scale = max(np.abs(vx).max(), np.abs(vy).max(), 1e-300)
+    assert np.max(np.abs(ux - vx)) <= 1e-12 * scale and np.max(np.abs(uy - vy)) <= 1e-12 * scale
+    Mr = ref.mass()
+    assert np.all(np.abs(M - Mr) <= 1e-12 * Mr)
+
+
+def test_fp64_fronts_and_log_match_oracle():
+    geom = W.capillary_geometry(128, 26, 32, 96, 0, 25)
+    prm = W.params(1.2, 1.0, 1.0, -0.15, 0.0)
+    nA, nB = W.slab_fields(geom, 0, 48)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", log_every=25,
+                 log_capacity=64) as lat:
+        want = []
+        for k in range(8):
+            want.append((ref.t, *ref.interface(), *ref.mass()))
+            ref.step(25)
+        want.append((ref.t, *ref.interface(), *ref.mass()))
+        lat.step(200)
+        log = lat.log()
+        z = lat.interface()
+    want = np.array(want)
+    assert log.shape == want.shape
+    assert np.array_equal(log[:, 0], want[:, 0])
+    assert np.max(np.abs(log[:, 1:4] - want[:, 1:4])) <= 1e-10
+    assert np.all(np.abs(log[:, 4:] - want[:, 4:]) <= 1e-12 * want[:, 4:])
+    assert np.max(np.abs(z - ref.interface())) <= 1e-10
+
+
+def test_fp64_capillary_256x32_3000_steps_matches_oracle():
+    c = W.config_capillary_256x32()
+    prm = dict(c["params"], tau_B=1.0)
+    nA, nB = W.initial_fields(c)
+    ref = oracle.OracleLattice(c["geom"], prm, nA, nB)
+    ref.step(3000)
+    with Lattice(dict(geom=c["geom"], params=prm, init=c["init"]), precision="f64") as lat:
+        lat.step(3000)
+        gA, gB = lat.densities()
+        z = lat.interface()
+    fluid = ref.solid() == 0
+    rA, rB = ref.densities()
+    assert rel_err(gA, rA, fluid) <= 1e-12 and rel_err(gB, rB, fluid) <= 1e-12
+    assert np.max(np.abs(z - ref.interface())) <= 1e-10
+
+
+def test_analytic_slab_and_droplet_init_equal_field_init():
+    geom = W.capillary_geometry(50, 20, 10, 40, 0, 19)
+    prm = W.params(1.0, 1.0, 1.0)
+    for init, fields in ((("slab", 0, 17), W.slab_fields(geom, 0, 17)),
+                         (("droplet", 25.0, 9.5, 6.3), W.droplet_fields(geom, 25.0, 9.5, 6.3))):
+        with Lattice(dict(geom=geom, params=prm, init=init), precision="f64") as a, \
+                Lattice(dict(geom=geom, params=prm, init=("fields", *fields)), precision="f64") as b:
+            assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
+def test_results_independent_of_tiling_and_graphs(prec):
+    geom = W.capillary_geometry(333, 37, 50, 300, 2, 30)
+    prm = W.params(1.2, 1.0, 0.9, -0.1, 0.05)
+    run = dict(geom=geom, params=prm, init=("slab", 0, 120))
+    scheds = [((128, 16), 0, None), ((64, 1), -1, None), ((64, 3), 5, None), ((256, 37), 0, None),
+              ((128, 100), 7, None)]
+    if prec != "f16s":
+        scheds += [((128, 16), 0, (1, 4)), ((64, 5), -1, (1, 3)), ((256, 8), 3, (1, 4)), ((64, 40), 0, (1, 4))]
+    outs = []
+    for tile, chunk, kern in scheds:
+        with Lattice(run, precision=prec, tile=tile, graph_chunk=chunk, rho_ref=(1.0, 1.0), kernel=kern) as lat:
+            if kern is not None:
+                assert lat.schedule == (tile[0], tile[1], kern[0], kern[1])
+            lat.step(23)
+            outs.append(lat.populations())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
+
+
+def test_async_kernel_fp64_matches_oracle():
+    geom, prm, kind = CASES["capillary64x18"]
+    nA, nB = _fields(geom, kind)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(50)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=(64, 5),
+                 kernel=(1, 4)) as lat:
+        lat.step(50)
+        F = lat.populations()
+    assert np.array_equal(F, ref.populations())
+
+
+def test_batched_runs_equal_solo_runs():
+    runs = []
+    for j, (L, H) in enumerate(((40, 6), (100, 13), (65, 30), (7, 3))):
+        r = W.capillary_run(L, H, 1.0 + 0.05 * j, 1.0, 0.8 + 0.1 * j, -0.1 * j)
+        runs.append(r)
+    with Lattice(runs, precision="f32", tile=(64, 8)) as bat:
+        bat.step(40)
+        batched = [bat.populations(r) for r in range(len(runs))]
+        zs = [bat.interface(r) for r in range(len(runs))]
+        ms = [bat.mass(r) for r in range(len(runs))]
+    for r, run in enumerate(runs):
+        with Lattice(run, precision="f32", tile=(128, 16)) as solo:
+            solo.step(40)
+            assert np.array_equal(solo.populations(), batched[r])
+            assert np.array_equal(solo.interface(), zs[r])
+            assert np.array_equal(solo.mass(), ms[r])
+
+
+def test_autotune_keeps_results():
+    geom = W.capillary_geometry(512, 34, 128, 512, 0, 33)
+    run = dict(geom=geom, params=W.params(1.2, 1.0, 1.0, -0.1), init=("slab", 0, 200))
+    with Lattice(run, precision="f32", autotune=True) as a, Lattice(run, precision="f32") as b:
+        a.step(120)
+        b.step(120)
+        assert a.t == b.t == 120
+        assert np.array_equal(a.populations(), b.populations())
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    geom = W.capillary_geometry(96, 20, 24, 72, 0, 19)
+    run = dict(geom=geom, params=W.params(1.2, 1.0, 0.9, -0.1), init=("slab", 0, 40))
+    path = os.path.join(tmp_path, "ck.bin")
+    with Lattice(run, precision="f32", log_every=10, log_capacity=32) as a:
+        a.step(50)
+        a.save(path)
+        a.step(50)
+        want, want_log, want_u = a.populations(), a.log(), a.velocity()
+    from paper_0807_0602_gb300.lbm import Lattice as _L
+    b = _L.load(path)
+    assert b.t == 50
+    b.step(50)
+    assert np.array_equal(b.populations(), want)
+    assert np.array_equal(b.log(), want_log)
+    assert np.array_equal(b.velocity()[0], want_u[0])
+    b.close()
+
+
+def test_fp32_close_to_oracle_after_100_steps():
+    # Reading of "relative error on densities": the error is taken relative to
+    # the density scale, max |n_gpu - n_ref| / max |n_ref| per species.  The
+    # pointwise ratio at minor-phase nodes (n ~ 0.008 against 2.0) is
+    # ill-conditioned in FP32 (rounding of the major species enters the minor
+    # one through the cross force); it is recorded, with a looser bound.
+    geom, prm, _ = CASES["capillary64x18"]
+    nA, nB = W.slab_fields(geom, 0, 21)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(100)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f32") as lat:
+        lat.step(100)
+        gA, gB = lat.densities()
+        z = lat.interface()
+    fluid = ref.solid() == 0
+    rA, rB = ref.densities()
+    for g, r in ((gA, rA), (gB, rB)):
+        assert np.max(np.abs(g - r)[fluid]) / np.max(np.abs(r)) <= 1e-5
+        assert rel_err(g, r, fluid) <= 1e-3
+    assert np.max(np.abs(z - ref.interface())) <= 0.05
+
+
+def test_fp16s_storage_error_is_bounded():
+    geom, prm, _ = CASES["capillary64x18"]
+    nA, nB = W.slab_fields(geom, 0, 21)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(100)
+    fluid = ref.solid() == 0
+    rA, rB = ref.densities()
+    for rho_ref in ((0.0, 0.0), (1.0, 1.0)):
+        with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f16s", rho_ref=rho_ref) as lat:
+            lat.step(100)
+            gA, gB = lat.densities()
+            M = lat.mass()
+        assert np.max(np.abs(gA - rA)[fluid]) < 2e-2 and np.max(np.abs(gB - rB)[fluid]) < 2e-2
+        assert np.all(np.abs(M - ref.mass()) < 1e-2 * ref.mass())
+
+
+def test_nonfinite_state_is_reported():
+    from paper_0807_0602_gb300 import _lib as L
+    geom = W.periodic_box(20, 6)
+    nA, nB = W.random_fields(geom, 1, 0.2, 1.0)
+    nA[3, 7] = np.nan
+    with Lattice(dict(geom=geom, params=W.params(1.0, 1.0, 1.0), init=("fields", nA, nB)), precision="f32") as lat:
+        lat.step(2)
+        with pytest.raises(L.LbmError) as e:
+            lat.mass()
+        assert e.value.code == L.LBM_ENONFINITE
+        assert lat.status() == L.LBM_ENONFINITE
+
+
+def test_full_size_capillary_8192x160_first_steps_match_oracle():
+    c = W.config_capillary_8192x160(tau_B=1.0)
+    nA, nB = W.initial_fields(c)
+    ref = oracle.OracleLattice(c["geom"], c["params"], nA, nB)
+    ref.step(3)
+    fluid = ref.solid() == 0
+    rA, rB = ref.densities()
+    with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision="f64") as lat:
+        lat.step(3)
+        gA, gB = lat.densities()
+    assert rel_err(gA, rA, fluid) <= 1e-12 and rel_err(gB, rB, fluid) <= 1e-12
+    for kern in (None, (1, 4)):
+        with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision="f32", tile=(128, 16),
+                     kernel=kern) as lat:
+            lat.step(3)
+            gA, gB = lat.densities()
+        for g, r in ((gA, rA), (gB, rB)):
+            assert np.max(np.abs(g - r)[fluid]) / np.max(np.abs(r)) <= 1e-5
