@@ -227,6 +227,23 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """Steps the workload with a fixed schedule and no graphs, for profilers."""
+    import torch
+    from paper_0807_0602_gb300.build import build as build_lib
+    from paper_0807_0602_gb300.lbm import Lattice
+    build_lib()
+    c = workload()
+    w, h, k, d = (int(v) for v in args.schedule.split(","))
+    with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision=args.precision, tile=(w, h),
+                 kernel=(k, d), graph_chunk=-1) as lat:
+        lat.step(args.profile)
+        lat.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_steps": args.profile, "schedule": [w, h, k, d], "precision": args.precision}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,9 +252,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="only step the workload this many times (for ncu captures) and exit")
+    ap.add_argument("--schedule", default="128,16,0,4",
+                    help="tile_w,tile_h,kernel,depth used by --profile")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     args.warmup = max(3, args.warmup)
 
     world, rank, local = dist_setup(args.gpus)
