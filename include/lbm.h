@@ -253,6 +253,39 @@ int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 int lbm_save(lbm_t* h, const char* path);
 int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
 
+/* Per-species FP64 mass of one population buffer, computed without
+ * allocating any memory.  The paper has no counterpart: this is plumbing for
+ * callers that cannot allocate device memory where they need the sums, for
+ * instance code running while a CUDA graph is being captured (where
+ * cudaMalloc is not permitted), a callback of a caching allocator that must
+ * not re-enter it, or a process whose device memory is entirely reserved by
+ * another framework's pool.  It computes what lbm_mass computes, in the same
+ * order, from a caller-owned buffer instead of a handle.
+ *
+ * g           geometry of the run: nx, ny, the plates (cap_x0, cap_x1, y_bot,
+ *             y_top); solid_mask must be NULL (LBM_EINVAL otherwise); the
+ *             init fields are ignored.
+ * precision   LBM_F64 / LBM_F32 / LBM_F16S: element type of populations.
+ * populations device buffer [2][9][ny][pitch] in the layout of lbm_run_info
+ *             (for a handle: lbm_run_info.base[current]); pitch >= nx.
+ * rho_ref     FP16S shift per species (NULL = 0); ignored otherwise.
+ * mass        device double[2] receiving (M_A, M_B); caller-owned.
+ * stream      cudaStream_t of the work (NULL = legacy default stream).
+ *
+ * Limit: ny <= LBM_NOALLOC_MAX_ROWS rows (LBM_EINVAL beyond it).  The per-row
+ * partial sums live in one fixed device array of 2 * LBM_NOALLOC_MAX_ROWS
+ * doubles (1 MiB) that every GPU loading the library holds until the process
+ * exits.  All calls on a device share that array: calls whose work overlaps
+ * on the GPU (different streams, or concurrent host threads) race and must
+ * be serialised by the caller; a call overwrites every row it reads, so
+ * nothing carries over from one call to the next.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  No memory is allocated or
+ * freed.  Asynchronous; returns LBM_ECUDA if the look-up or a launch fails. */
+#define LBM_NOALLOC_MAX_ROWS 65536
+int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void* populations, int pitch,
+                     const double rho_ref[2], double* mass, void* stream);
+
 /* Sticky device status of the handle (synchronises). */
 int lbm_status(lbm_t* h);
 

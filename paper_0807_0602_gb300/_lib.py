@@ -76,6 +76,8 @@ SIGNATURES = {
     "lbm_set_schedule": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [ctypes.c_char_p, P(Options), P(c_void_p)]),
+    "lbm_mass_noalloc": (ctypes.c_int, [P(Geometry), ctypes.c_int, c_void_p, ctypes.c_int, P(c_double), c_void_p,
+                                        c_void_p]),
     "lbm_status": (ctypes.c_int, [c_void_p]),
     "lbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_destroy": (None, [c_void_p]),

@@ -26,6 +26,7 @@ UNITS = {
     "kernels_f32.cu": [],
     "lbm_capi.cu": [],
     "mlp.cu": [],
+    "lbm_noalloc.cu": [],
 }
 
 
