@@ -287,7 +287,7 @@ def main():
     with torch.cuda.stream(stream):
         lat = Lattice(run, precision=args.precision, log_every=log_every, log_capacity=4096, autotune=True,
                       stream=stream)
-        lat.step(100)          # autotuning: real steps, every tiling gives the same bits
+        lat.step(400)          # autotuning: real steps, every schedule gives the same bits
         lat.step(args.warmup)
         lat.sync()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
@@ -315,7 +315,7 @@ def main():
         kernel_ms = statistics.mean(kern)
         M = lat.mass()
         finite = bool(np.all(np.isfinite(M)))
-        tile = lat.tiling
+        sched = lat.schedule
         lat.close()
 
     total_ms = max_over_ranks(world, total_ms)
@@ -332,7 +332,8 @@ def main():
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         lat2 = Lattice(dict(geom=g, params=c["params"], init=("fields", hA.numpy(), hB.numpy())),
-                       precision=args.precision, log_every=log_every, log_capacity=4096, tile=tile, stream=stream)
+                       precision=args.precision, log_every=log_every, log_capacity=4096, tile=sched[:2],
+                       kernel=sched[2:], stream=stream)
         lat2.step(args.steps)
         log = lat2.log()
         dA, dB = lat2.densities()
@@ -358,7 +359,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [g["nx"], g["ny"]], "fluid_nodes": fluid_nodes,
-                   "precision": args.precision, "tile": list(tile), "log_every": log_every,
+                   "precision": args.precision, "tile": list(sched[:2]),
+                   "step_kernel": ["register", "cp.async", "tma"][sched[2]], "log_every": log_every,
                    "l2": "flushed (256 MB write) between timed steps", "state_finite": finite,
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,

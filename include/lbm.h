@@ -141,8 +141,12 @@ typedef struct lbm_options {
  * populations).  Populations of buffer b live at
  *   base[b] + ((k * 9 + i) * ny + y) * pitch + x      (elements)
  * for species k (0 = A, 1 = B), direction i of Eq. 6 in the order
- * 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
- * current is the buffer holding the post-collision populations of time t. */
+ * 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1),
+ * 0 <= x < nx.  Each row also stores the periodic images of columns nx - 1
+ * and 0 at x = -1 and x = nx (ghost columns); a row starts LBM_COL0 elements
+ * before base + row offset.  current is the buffer holding the
+ * post-collision populations of time t. */
+#define LBM_COL0 8
 typedef struct lbm_run_info {
     int32_t nx, ny, pitch, precision;
     int32_t current;
@@ -239,10 +243,14 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 /* Full schedule of the step kernel: tiling plus the kernel variant
  * (LBM_KERNEL_REGISTER: pulled populations through registers;
  * LBM_KERNEL_ASYNC: through a depth-stage cp.async ring in shared memory,
- * depth 3 or 4; not available for LBM_F16S).  Results do not depend on it.
- * lbm_set_schedule returns LBM_EINVAL for an unsupported combination. */
+ * depth 3 or 4, not available for LBM_F16S; LBM_KERNEL_TMA: source rows
+ * streamed into a shared-memory ring by bulk copies (cp.async.bulk with
+ * mbarrier completion), all precisions, every run needs nx >= 4; depth is
+ * ignored).  Results do not depend on the schedule.  lbm_set_schedule
+ * returns LBM_EINVAL for an unsupported combination. */
 #define LBM_KERNEL_REGISTER 0
 #define LBM_KERNEL_ASYNC 1
+#define LBM_KERNEL_TMA 2
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 
@@ -266,8 +274,10 @@ int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
  *             y_top); solid_mask must be NULL (LBM_EINVAL otherwise); the
  *             init fields are ignored.
  * precision   LBM_F64 / LBM_F32 / LBM_F16S: element type of populations.
- * populations device buffer [2][9][ny][pitch] in the layout of lbm_run_info
- *             (for a handle: lbm_run_info.base[current]); pitch >= nx.
+ * populations device buffer [2][9][ny][pitch] in the layout of lbm_run_info,
+ *             pointing at column 0 of row 0 (for a handle:
+ *             lbm_run_info.base[current]); pitch >= nx (only columns
+ *             0 <= x < nx are read).
  * rho_ref     FP16S shift per species (NULL = 0); ignored otherwise.
  * mass        device double[2] receiving (M_A, M_B); caller-owned.
  * stream      cudaStream_t of the work (NULL = legacy default stream).

@@ -5,28 +5,15 @@
 
 namespace sc {
 
-__global__ void __launch_bounds__(256) k_mass_final(const RunDesc* __restrict__ runs,
-                                                    const double* __restrict__ partials, double* __restrict__ mass,
-                                                    LogCtl lc, int write_log, uint32_t* __restrict__ err) {
+__global__ void __launch_bounds__(kMassThreads) k_mass_final(const RunDesc* __restrict__ runs,
+                                                             const double* __restrict__ partials,
+                                                             double* __restrict__ mass, LogCtl lc, int write_log,
+                                                             uint32_t* __restrict__ err) {
     const RunDesc& rd = runs[blockIdx.x];
-    double a = 0.0, b = 0.0;
-    for (int y = threadIdx.x; y < rd.ny; y += 256) {
-        a = __dadd_rn(a, partials[2 * (rd.row0 + y) + 0]);
-        b = __dadd_rn(b, partials[2 * (rd.row0 + y) + 1]);
-    }
-    __shared__ double s[2][256];
-    s[0][threadIdx.x] = a;
-    s[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
-            s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
-        }
-        __syncthreads();
-    }
+    __shared__ double tot[2];
+    mass_rows_total(rd.ny, partials + 2 * rd.row0, tot);
     if (threadIdx.x == 0) {
-        const double MA = s[0][0], MB = s[1][0];
+        const double MA = tot[0], MB = tot[1];
         if (mass) {
             mass[2 * blockIdx.x + 0] = MA;
             mass[2 * blockIdx.x + 1] = MB;

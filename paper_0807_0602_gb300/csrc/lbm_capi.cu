@@ -43,7 +43,7 @@ struct lbm_s {
     size_t d_tiles_cap = 0;
     std::vector<int> tile_begin, tile_count;
     int tile_w = 128, tile_h = 16;
-    int kvar = 0, depth = 4;       // step kernel: 0 = register pull, 1 = cp.async stages of depth D
+    int kvar = 0, depth = 4;       // step kernel: 0 register pull, 1 cp.async stages of depth D, 2 TMA ring
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -141,13 +141,17 @@ int validate_options(const lbm_options& o) {
     return LBM_OK;
 }
 
-int round_pitch(int nx) { return (nx + 63) / 64 * 64; }
+// Rows hold LBM_COL0 elements before column 0 (ghost image of column nx - 1
+// at x = -1) and at least LBM_COL0 after column nx - 1 (image of column 0 at
+// x = nx); buffers point at column 0 of row 0.
+int round_pitch(int nx) { return (nx + 2 * LBM_COL0 + 63) / 64 * 64; }
 
 void build_tiles(lbm_t* h, int W, int R) {
     h->tiles.clear();
     h->tile_begin.assign(h->nruns, 0);
     h->tile_count.assign(h->nruns, 0);
-    const int Wc = W - 2;
+    // the TMA kernel collides W - 8 columns from x0 multiple of 8, the others W - 2
+    const int Wc = h->kvar == 2 ? W - 8 : W - 2;
     for (int r = 0; r < h->nruns; ++r) {
         const RunDesc& rd = h->runs[r];
         const int Rr = std::max(1, std::min(R, rd.ny));
@@ -196,13 +200,21 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     if (h->kvar == 1)
         return dispatch(h->precision,
                         [&](auto L) { return L.step_async(W, h->depth, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 2)
+        return dispatch(h->precision,
+                        [&](auto L) { return L.step_tma(W, h->d_runs, h->d_tiles, nt, parity, h->d_err, s); });
     return dispatch(h->precision, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
     if (W != 64 && W != 128 && W != 256) return false;
-    if (R < 1 || kvar < 0 || kvar > 1) return false;
+    if (R < 1 || kvar < 0 || kvar > 2) return false;
     if (kvar == 1 && (h->precision == LBM_F16S || (depth != 3 && depth != 4))) return false;
+    if (kvar == 2) {
+        // the TMA windows rely on two ghost columns each side: nx >= 4
+        for (const RunDesc& rd : h->runs)
+            if (rd.nx < 4) return false;
+    }
     return true;
 }
 
@@ -291,15 +303,13 @@ int autotune(lbm_t* h, int64_t* n) {
     std::sort(Rs.begin(), Rs.end());
     Rs.erase(std::unique(Rs.begin(), Rs.end()), Rs.end());
     std::vector<Cand> cands;
-    for (int W : {64, 128})
+    for (int W : {64, 128, 256})
         for (int R : Rs) {
             cands.push_back({W, R, 0, 4});
-            if (h->precision != LBM_F16S) {
-                cands.push_back({W, R, 1, 3});
-                cands.push_back({W, R, 1, 4});
-            }
+            if (schedule_ok(h, W, R, 2, 4)) cands.push_back({W, R, 2, 4});
+            if (W < 256 && schedule_ok(h, W, R, 1, 4)) cands.push_back({W, R, 1, 4});
         }
-    const int per = 3;
+    const int per = 6;
     if (*n < (int64_t)cands.size() * (per + 1)) return LBM_OK;  // too short to tune now
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
@@ -418,8 +428,8 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
         rd.plane = (long long)gr.ny * rd.pitch;
         const size_t buf = (size_t)18 * gr.ny * rd.pitch * h->elem;
         const size_t bufa = (buf + 255) & ~size_t(255);
-        rd.buf[0] = arena + off[r];
-        rd.buf[1] = arena + off[r] + bufa;
+        rd.buf[0] = arena + off[r] + (size_t)LBM_COL0 * h->elem;
+        rd.buf[1] = arena + off[r] + bufa + (size_t)LBM_COL0 * h->elem;
         rd.cap_x0 = gr.cap_x0;
         rd.cap_x1 = gr.cap_x1;
         rd.y_bot = gr.y_bot;

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_fp16.h>
+
+#include "lbm.h"
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +59,8 @@ struct Launch {
                             cudaStream_t s);
     static cudaError_t step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s);
+    static cudaError_t step_tma(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                uint32_t* err, cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
     static cudaError_t densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA,

@@ -50,13 +50,34 @@ template <> struct Wt<float> {
     static constexpr float w0 = 4.0f / 9.0f, w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
 };
 
+// Arithmetic of the collision, spelled out so that no kernel variant can
+// contract it differently: FP64 uses separately rounded products and sums in
+// the canonical order (fma(a, b, c) = (a b) + c, two roundings); FP32 fuses
+// exactly those products into FMAs.  Every step kernel therefore produces the
+// same bits for a given precision, whatever its schedule.
+template <typename C> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+
 // Storage <-> compute conversion.  FP16S stores f - w_i rho_ref,k.
 __device__ __forceinline__ double dec(double v, double) { return v; }
 __device__ __forceinline__ float dec(float v, float) { return v; }
-__device__ __forceinline__ float dec(__half v, float sh) { return __half2float(v) + sh; }
+__device__ __forceinline__ float dec(__half v, float sh) { return __fadd_rn(__half2float(v), sh); }
 __device__ __forceinline__ void enc(double* p, double v, double) { *p = v; }
 __device__ __forceinline__ void enc(float* p, float v, float) { *p = v; }
-__device__ __forceinline__ void enc(__half* p, float v, float sh) { *p = __float2half_rn(v - sh); }
+__device__ __forceinline__ void enc(__half* p, float v, float sh) { *p = __float2half_rn(__fsub_rn(v, sh)); }
 
 template <typename S> __device__ __forceinline__ S ldg(const S* p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ldg<__half>(const __half* p) {
@@ -145,7 +166,10 @@ __device__ __forceinline__ void pull_node(const S* __restrict__ src, long long p
 
 template <typename C>
 __device__ __forceinline__ C dens9(const C (&f)[9]) {
-    return ((((((((f[0] + f[1]) + f[2]) + f[3]) + f[4]) + f[5]) + f[6]) + f[7]) + f[8]);
+    using A = Ar<C>;
+    return A::add(A::add(A::add(A::add(A::add(A::add(A::add(A::add(f[0], f[1]), f[2]), f[3]), f[4]), f[5]), f[6]),
+                         f[7]),
+                  f[8]);
 }
 
 struct RowIdx {
@@ -186,70 +210,97 @@ struct StepCtx {
 // ring (slots of rows r-1, r, r+1), the node's pulled populations from fc.
 // MODE 0 writes the post-collision populations, MODE 1 the whole-fluid
 // velocity rho u = sum_k j_k + (1/2) sum_k n_k a_k.
+// Offsets from column x to its ghost images: columns 0 and 1 are mirrored at
+// nx and nx + 1, columns nx - 2 and nx - 1 at -2 and -1 (0 = no image).
+__device__ __forceinline__ int ghost_r(int x, int nx) { return x < 2 ? nx : 0; }
+__device__ __forceinline__ int ghost_l(int x, int nx) { return x >= nx - 2 ? -nx : 0; }
+
+// Populations of columns 0, 1 and nx - 2, nx - 1 are also written to their
+// periodic images at x = nx, nx + 1 and x = -2, -1 (ghost columns), so that
+// every source row a later step reads is one contiguous window; gr / gl give
+// the offsets of those images from the node (0 = none).
 template <typename S, int W, int MODE>
 __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
                                              const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
                                              S* __restrict__ dst, long long plane, long long o, MomOut mo,
-                                             long long mo_idx) {
+                                             long long mo_idx, int gr = 0, int gl = 0) {
     using C = typename Prec<S>::C;
     using Wc = Wt<C>;
+    using A = Ar<C>;
     C n[2], jx[2], jy[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const C(&f)[9] = fc[k];
         n[k] = sd[s_0][k][t];
-        jx[k] = ((((f[1] - f[3]) + f[5]) - f[6]) - f[7]) + f[8];
-        jy[k] = ((((f[2] - f[4]) + f[5]) + f[6]) - f[7]) - f[8];
+        jx[k] = A::add(A::sub(A::sub(A::add(A::sub(f[1], f[3]), f[5]), f[6]), f[7]), f[8]);
+        jy[k] = A::sub(A::sub(A::add(A::add(A::sub(f[2], f[4]), f[5]), f[6]), f[7]), f[8]);
     }
     // wall sum of Eq. 11, the same for both species
     C Wx = C(0), Wy = C(0);
     if (m) {
-        if (SOL(m, 0, 1)) Wx = Wx + Wc::w1;                           // i = 1
-        if (SOL(m, 1, 0)) Wy = Wy + Wc::w1;                           // i = 2
-        if (SOL(m, 0, -1)) Wx = Wx - Wc::w1;                          // i = 3
-        if (SOL(m, -1, 0)) Wy = Wy - Wc::w1;                          // i = 4
-        if (SOL(m, 1, 1)) { Wx = Wx + Wc::w5; Wy = Wy + Wc::w5; }     // i = 5
-        if (SOL(m, 1, -1)) { Wx = Wx - Wc::w5; Wy = Wy + Wc::w5; }    // i = 6
-        if (SOL(m, -1, -1)) { Wx = Wx - Wc::w5; Wy = Wy - Wc::w5; }   // i = 7
-        if (SOL(m, -1, 1)) { Wx = Wx + Wc::w5; Wy = Wy - Wc::w5; }    // i = 8
+        if (SOL(m, 0, 1)) Wx = A::add(Wx, Wc::w1);                                // i = 1
+        if (SOL(m, 1, 0)) Wy = A::add(Wy, Wc::w1);                                // i = 2
+        if (SOL(m, 0, -1)) Wx = A::sub(Wx, Wc::w1);                               // i = 3
+        if (SOL(m, -1, 0)) Wy = A::sub(Wy, Wc::w1);                               // i = 4
+        if (SOL(m, 1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }   // i = 5
+        if (SOL(m, 1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }  // i = 6
+        if (SOL(m, -1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); } // i = 7
+        if (SOL(m, -1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); }  // i = 8
     }
-    // bulk force of Eq. 9 from the neighbour densities of the other species
+    // bulk force of Eq. 9 from the neighbour densities of the other species:
+    // S = ((((w1 n1 - w1 n3) + w5 n5) - w5 n6) - w5 n7) + w5 n8 (and y)
     C ax[2], ay[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int kb = 1 - k;
         const C n1 = sd[s_0][kb][t + 1], n2 = sd[s_p][kb][t], n3 = sd[s_0][kb][t - 1], n4 = sd[s_m][kb][t],
                 n5 = sd[s_p][kb][t + 1], n6 = sd[s_p][kb][t - 1], n7 = sd[s_m][kb][t - 1], n8 = sd[s_m][kb][t + 1];
-        const C Sx = ((((Wc::w1 * n1 - Wc::w1 * n3) + Wc::w5 * n5) - Wc::w5 * n6) - Wc::w5 * n7) + Wc::w5 * n8;
-        const C Sy = ((((Wc::w1 * n2 - Wc::w1 * n4) + Wc::w5 * n5) + Wc::w5 * n6) - Wc::w5 * n7) - Wc::w5 * n8;
-        ax[k] = (-(cx.G * Sx) - (cx.Gw[k] * Wx)) + cx.gx;
-        ay[k] = (-(cx.G * Sy) - (cx.Gw[k] * Wy)) + cx.gy;
+        C Sx = A::fma(-Wc::w1, n3, A::mul(Wc::w1, n1));
+        Sx = A::fma(Wc::w5, n5, Sx);
+        Sx = A::fma(-Wc::w5, n6, Sx);
+        Sx = A::fma(-Wc::w5, n7, Sx);
+        Sx = A::fma(Wc::w5, n8, Sx);
+        C Sy = A::fma(-Wc::w1, n4, A::mul(Wc::w1, n2));
+        Sy = A::fma(Wc::w5, n5, Sy);
+        Sy = A::fma(Wc::w5, n6, Sy);
+        Sy = A::fma(-Wc::w5, n7, Sy);
+        Sy = A::fma(-Wc::w5, n8, Sy);
+        ax[k] = A::add(A::sub(-A::mul(cx.G, Sx), A::mul(cx.Gw[k], Wx)), cx.gx);
+        ay[k] = A::add(A::sub(-A::mul(cx.G, Sy), A::mul(cx.Gw[k], Wy)), cx.gy);
     }
     if (MODE == 1) {
-        mo.ux[mo_idx] = (double)(((jx[0] + jx[1]) + C(0.5) * ((n[0] * ax[0]) + (n[1] * ax[1]))) / (n[0] + n[1]));
-        mo.uy[mo_idx] = (double)(((jy[0] + jy[1]) + C(0.5) * ((n[0] * ay[0]) + (n[1] * ay[1]))) / (n[0] + n[1]));
+        const C ntot = A::add(n[0], n[1]);
+        const C fxs = A::fma(n[0], ax[0], A::mul(n[1], ax[1]));
+        const C fys = A::fma(n[0], ay[0], A::mul(n[1], ay[1]));
+        mo.ux[mo_idx] = (double)A::div(A::fma(C(0.5), fxs, A::add(jx[0], jx[1])), ntot);
+        mo.uy[mo_idx] = (double)A::div(A::fma(C(0.5), fys, A::add(jy[0], jy[1])), ntot);
         return;
     }
     // common velocity (Eq. 8) and shifted equilibrium velocities (Eq. 7)
-    const C den = n[0] * cx.itau[0] + n[1] * cx.itau[1];
-    const C Ux = (jx[0] * cx.itau[0] + jx[1] * cx.itau[1]) / den;
-    const C Uy = (jy[0] * cx.itau[0] + jy[1] * cx.itau[1]) / den;
+    const C den = A::fma(n[0], cx.itau[0], A::mul(n[1], cx.itau[1]));
+    const C Ux = A::div(A::fma(jx[0], cx.itau[0], A::mul(jx[1], cx.itau[1])), den);
+    const C Uy = A::div(A::fma(jy[0], cx.itau[0], A::mul(jy[1], cx.itau[1])), den);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const C ux = Ux + cx.tau[k] * ax[k];
-        const C uy = Uy + cx.tau[k] * ay[k];
-        const C usq = ux * ux + uy * uy;
-        const C b = C(1.5) * usq;
-        const C wn0 = Wc::w0 * n[k], wn1 = Wc::w1 * n[k], wn5 = Wc::w5 * n[k];
-        const C cu[9] = {C(0), ux, uy, -ux, -uy, ux + uy, -ux + uy, -ux - uy, ux - uy};
+        const C ux = A::fma(cx.tau[k], ax[k], Ux);
+        const C uy = A::fma(cx.tau[k], ay[k], Uy);
+        const C usq = A::fma(ux, ux, A::mul(uy, uy));
+        const C b = A::mul(C(1.5), usq);
+        const C wn0 = A::mul(Wc::w0, n[k]), wn1 = A::mul(Wc::w1, n[k]), wn5 = A::mul(Wc::w5, n[k]);
+        const C cu[9] = {C(0), ux, uy, -ux, -uy, A::add(ux, uy), A::add(-ux, uy), A::sub(-ux, uy), A::sub(ux, uy)};
         S* d = dst + (long long)k * 9 * plane + o;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
             const C c = cu[i];
-            const C feq = wn * (((C(1) + C(3) * c) + C(4.5) * (c * c)) - b);   // Eqs. 3-5
+            // Eqs. 3-5: wn (((1 + 3 c) + 4.5 (c c)) - b)
+            const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
             const C f = fc[k][i];
-            enc(d + (long long)i * plane, f - (f - feq) * cx.itau[k], cx.sh.v[k][grp(i)]);   // Eq. 2
+            S* p = d + (long long)i * plane;
+            const C fnew = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
+            enc(p, fnew, cx.sh.v[k][grp(i)]);
+            if (gr) enc(p + gr, fnew, cx.sh.v[k][grp(i)]);
+            if (gl) enc(p + gl, fnew, cx.sh.v[k][grp(i)]);
         }
     }
 }
@@ -325,7 +376,8 @@ __global__ void __launch_bounds__(W) k_step(const RunDesc* __restrict__ runs, co
             const RowIdx q = rows_of(r, ny);
             if (!SOL(smc, 0, 0))
                 collide_node<S, W, MODE>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane,
-                                         (long long)q.rw * pitch + sc.xc, mo, (long long)q.rw * mo.nx + sc.xc);
+                                         (long long)q.rw * pitch + sc.xc, mo, (long long)q.rw * mo.nx + sc.xc,
+                                         ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
             else if (MODE == 1) {
                 mo.ux[(long long)q.rw * mo.nx + sc.xc] = 0.0;
                 mo.uy[(long long)q.rw * mo.nx + sc.xc] = 0.0;
@@ -450,7 +502,7 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
         if (sc.coll && !SOL(smc, 0, 0)) {
             const RowIdx q = rows_of(r, ny);
             collide_node<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (long long)q.rw * pitch + sc.xc,
-                                  MomOut{nullptr, nullptr, 0}, 0);
+                                  MomOut{nullptr, nullptr, 0}, 0, ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -459,6 +511,227 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
         smc = smn;
     }
     cp_wait<0>();
+}
+
+// ---- TMA-staged variant ------------------------------------------------------
+// One elected thread streams every source row the CTA needs into an S-slot
+// ring of shared memory with bulk copies (cp.async.bulk, one per population
+// plane and row: a contiguous window of the row thanks to the ghost columns),
+// completing on one mbarrier per slot; the copies run P rows ahead of the row
+// being pulled, so HBM reads are in flight without holding registers.
+// Threads then pull from shared memory at fixed offsets.
+//
+// Column mapping: a CTA collides the Wc = W - 8 columns [x0, x0 + Wc)
+// (x0 a multiple of 8, so global stores of a warp start on a 32-byte
+// sector); thread t < Wc owns column x0 + t, threads Wc and Wc + 1 supply the
+// densities of the halo columns x0 - 1 and x0 + Wc.  The density ring is
+// indexed by column offset j + 1 (j in [-1, Wc]).
+//
+// Every mbarrier wait is bounded: a thread that gives up sets a flag, the
+// per-row __syncthreads_or makes the exit block-uniform, the CTA drains the
+// copies it issued (bounded again) and records ERR_TIMEOUT.
+constexpr int kTmaSlots = 5;           // S: ring slots (source rows)
+constexpr int kTmaAhead = 5;           // P: rows issued ahead of the first needed one
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s of SM clock per wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (by elapsed SM cycles, whatever each try_wait suspends for);
+// returns false if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long start = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - start > kWaitCycles) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename S, int W>
+struct TmaGeom {
+    static constexpr int Wc = W - 8;                      // collided columns per CTA
+    static constexpr int OFF = 16 / (int)sizeof(S);       // window starts OFF columns before x0
+    static constexpr int WIN = Wc + 2 * OFF;              // window width (elements), 16-byte multiple
+    static constexpr size_t slot_elems = (size_t)18 * WIN;
+    static constexpr size_t smem_bytes() {
+        return (size_t)kTmaSlots * slot_elems * sizeof(S) + 4 * 2 * W * sizeof(typename Prec<S>::C) +
+               kTmaSlots * sizeof(uint64_t) + 16;
+    }
+};
+
+template <typename S, int W>
+__global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
+                                                int parity, uint32_t* __restrict__ err) {
+    using C = typename Prec<S>::C;
+    using TG = TmaGeom<S, W>;
+    constexpr int Wc = TG::Wc, OFF = TG::OFF, WIN = TG::WIN;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S* ring = reinterpret_cast<S*>(smem_raw);                                         // [S][18][WIN]
+    C(*sd)[2][W] = reinterpret_cast<C(*)[2][W]>(smem_raw + kTmaSlots * TG::slot_elems * sizeof(S));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kTmaSlots * TG::slot_elems * sizeof(S) +
+                                                 4 * 2 * W * sizeof(C));
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const int x0 = tl.x0, y0 = tl.y0, y1 = tl.y1;
+    const int ncols = min(Wc, nx - x0);
+    // column of this thread: j in [-1, ncols] (density), -2 = idle
+    int j = -2;
+    if (t < ncols) j = t;
+    else if (t == Wc) j = -1;
+    else if (t == Wc + 1) j = ncols;
+    const bool dcol = j >= -1;
+    const bool coll = j >= 0 && j < ncols;
+    int xc = x0 + j;
+    if (xc < 0) xc += nx;
+    else if (xc >= nx) xc -= nx;
+    if (!dcol) xc = 0;
+    const int xm = xc == 0 ? nx - 1 : xc - 1;
+    const int xp = xc == nx - 1 ? 0 : xc + 1;
+    const int sdc = j + 1;                 // density ring column
+    const int wc = j + OFF;                // column of this node inside a window
+    // window bytes of one plane row, clipped to the allocated row
+    const int win_elems = min(WIN, (pitch - LBM_COL0) - (x0 - OFF));
+    const unsigned win_bytes = (unsigned)(win_elems * (int)sizeof(S));
+    const int nsrc = (y1 - y0) + 4;        // source rows y0 - 2 .. y1 + 1
+
+    if (t == 0) {
+        for (int s = 0; s < kTmaSlots; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    // source row sequence number sq (row y0 - 2 + sq) lives in slot sq % S;
+    // its k-th fill completes phase k & 1 of that slot's mbarrier
+    int issued = 0;   // meaningful in thread 0 only
+    auto issue_upto = [&](int last) {   // thread 0: issue every sq <= last not yet issued
+        for (; issued <= last && issued < nsrc; ++issued) {
+            const int sq = issued;
+            const int slot = sq % kTmaSlots;
+            int row = (y0 - 2 + sq) % ny;
+            if (row < 0) row += ny;
+            S* dslot = ring + (size_t)slot * TG::slot_elems;
+            mbar_expect_tx(&bars[slot], 18u * win_bytes);
+            const S* g = src + (long long)row * pitch + (x0 - OFF);
+#pragma unroll 1
+            for (int q = 0; q < 18; ++q)
+                bulk_g2s(dslot + q * WIN, g + (long long)q * plane, win_bytes, &bars[slot]);
+        }
+    };
+    bool timed_out = false;
+    auto wait_row = [&](int sq) {
+        if (sq < nsrc && !timed_out && !mbar_wait(&bars[sq % kTmaSlots], (unsigned)((sq / kTmaSlots) & 1)))
+            timed_out = true;
+    };
+    // pull of row p from source rows p - 1, p, p + 1 (sq = p - y0 + 1 .. + 3)
+    auto pull_row = [&](int p, C (&f)[2][9], unsigned& smask, int slot_d) {
+        const RowIdx q = rows_of(p, ny);
+        C nA = C(0), nB = C(0);
+        smask = 0;
+        if (dcol) {
+            smask = nbr_solid(geo, xm, xc, xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const int sqm = p - y0 + 1;
+                const S* Rm = ring + (size_t)(sqm % kTmaSlots) * TG::slot_elems + wc;
+                const S* R0 = ring + (size_t)((sqm + 1) % kTmaSlots) * TG::slot_elems + wc;
+                const S* Rp = ring + (size_t)((sqm + 2) % kTmaSlots) * TG::slot_elems + wc;
+                const unsigned m = smask;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int b = k * 9 * WIN;
+                    f[k][0] = dec(R0[b + 0 * WIN], cx.sh.v[k][0]);
+                    f[k][1] = dec(SOL(m, 0, -1) ? R0[b + 3 * WIN] : R0[b + 1 * WIN - 1], cx.sh.v[k][1]);
+                    f[k][2] = dec(SOL(m, -1, 0) ? R0[b + 4 * WIN] : Rm[b + 2 * WIN], cx.sh.v[k][1]);
+                    f[k][3] = dec(SOL(m, 0, 1) ? R0[b + 1 * WIN] : R0[b + 3 * WIN + 1], cx.sh.v[k][1]);
+                    f[k][4] = dec(SOL(m, 1, 0) ? R0[b + 2 * WIN] : Rp[b + 4 * WIN], cx.sh.v[k][1]);
+                    f[k][5] = dec(SOL(m, -1, -1) ? R0[b + 7 * WIN] : Rm[b + 5 * WIN - 1], cx.sh.v[k][2]);
+                    f[k][6] = dec(SOL(m, -1, 1) ? R0[b + 8 * WIN] : Rm[b + 6 * WIN + 1], cx.sh.v[k][2]);
+                    f[k][7] = dec(SOL(m, 1, 1) ? R0[b + 5 * WIN] : Rp[b + 7 * WIN + 1], cx.sh.v[k][2]);
+                    f[k][8] = dec(SOL(m, 1, -1) ? R0[b + 6 * WIN] : Rp[b + 8 * WIN - 1], cx.sh.v[k][2]);
+                }
+                nA = dens9(f[0]);
+                nB = dens9(f[1]);
+            }
+            sd[slot_d][0][sdc] = nA;
+            sd[slot_d][1][sdc] = nB;
+        }
+    };
+
+    C fc[2][9], fn[2][9];
+    unsigned smc = 0, smn = 0;
+    bool abort_cta = false;
+    // prologue: fill the whole ring, then pull rows y0 - 1 and y0 (sq 0..3)
+    if (t == 0) issue_upto(kTmaSlots - 1);
+    for (int sq = 0; sq < 4; ++sq) wait_row(sq);
+    if (!timed_out) {
+        pull_row(y0 - 1, fn, smn, 0);
+        pull_row(y0, fc, smc, 1);
+    }
+    // the prologue pulls must be done before thread 0 refills their slots
+    if (__syncthreads_or(timed_out)) abort_cta = true;
+    for (int r = y0; r < y1 && !abort_cta; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        // every thread finished the pulls that read source rows <= r - y0 + 1
+        // (previous barrier): refill their slots up to two rows past the next need
+        if (t == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue_upto(r - y0 + 6);
+        }
+        wait_row(r - y0 + 4);
+        if (!timed_out) pull_row(r + 1, fn, smn, s_p);
+        if (__syncthreads_or(timed_out)) {
+            abort_cta = true;
+            break;
+        }
+        if (coll && !SOL(smc, 0, 0)) {
+            const RowIdx q = rows_of(r, ny);
+            collide_node<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, sdc, dst, plane, (long long)q.rw * pitch + xc,
+                                  MomOut{nullptr, nullptr, 0}, 0, ghost_r(xc, nx), ghost_l(xc, nx));
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
+        smc = smn;
+    }
+    if (abort_cta && t == 0) {
+        // drain the copies this CTA issued before it exits (bounded): the last
+        // fill of each slot completes after every earlier one
+        for (int sq = max(0, issued - kTmaSlots); sq < issued; ++sq)
+            mbar_wait(&bars[sq % kTmaSlots], (unsigned)((sq / kTmaSlots) & 1));
+        atomicOr(err, ERR_TIMEOUT);
+    }
+    // without a timeout every issued row (sq < nsrc) was waited on by the loop
 }
 
 template <typename S, int W, int D>
@@ -505,8 +778,16 @@ __global__ void k_init(const RunDesc* __restrict__ runs) {
                 for (int i = 0; i < 9; ++i) {
                     const C w = i == 0 ? Wc::w0 : (i <= 4 ? Wc::w1 : Wc::w5);
                     S* p = base + ((long long)k * 9 + i) * rd.plane + o;
-                    if (sol) *p = S(0.0f);
-                    else enc(p, w * n, sh.v[k][grp(i)]);
+                    const int gr = ghost_r(x, rd.nx), gl = ghost_l(x, rd.nx);
+                    if (sol) {
+                        *p = S(0.0f);
+                        if (gr) p[gr] = S(0.0f);
+                        if (gl) p[gl] = S(0.0f);
+                    } else {
+                        enc(p, w * n, sh.v[k][grp(i)]);
+                        if (gr) enc(p + gr, w * n, sh.v[k][grp(i)]);
+                        if (gl) enc(p + gl, w * n, sh.v[k][grp(i)]);
+                    }
                 }
             }
         }
@@ -570,17 +851,23 @@ __global__ void k_import(const RunDesc* __restrict__ runs, int run, int parity, 
         const long long ki = q / rd.nodes;
         const int rem = (int)(q - ki * rd.nodes);
         const int y = rem / rd.nx, x = rem - y * rd.nx;
-        base[ki * rd.plane + (long long)y * rd.pitch + x] = in[q];
+        S* p = base + ki * rd.plane + (long long)y * rd.pitch + x;
+        *p = in[q];
+        const int gr = ghost_r(x, rd.nx), gl = ghost_l(x, rd.nx);
+        if (gr) p[gr] = in[q];
+        if (gl) p[gl] = in[q];
     }
 }
 
 // ---- fronts (Numerical Results section, Figs. 6-8) -------------------------
-// One CTA of 4 warps per run; warp w scans tracked row w from cap_x0:
+// One CTA of 4 x 256 threads per run; group w scans tracked row w from cap_x0:
 //   w = 0, 1: the centre row(s) with v = phi = (n_A - n_B)/(n_A + n_B);
 //   w = 2, 3: the fluid rows next to the bottom / top plate with
 //             v = n_A - rho_bulk / 3.
-// The first failing column x* (v < 0) comes from a warp ballot per 32-column
-// chunk; z = (x* - 1 - cap_x0) + v(x* - 1) / (v(x* - 1) - v(x*)), in FP64.
+// Thread t of a group tests columns cap_x0 + t, + 256, ... in increasing
+// order and keeps its first failing one (v < 0); a shared atomicMin gives the
+// first failing column x* of the row (order-free, so deterministic).  Then
+// z = (x* - 1 - cap_x0) + v(x* - 1) / (v(x* - 1) - v(x*)) in FP64.
 template <typename S>
 __device__ __forceinline__ double front_value(const RunDesc& rd, const S* base, const Shift<S>& sh, int x,
                                               int y, bool prec) {
@@ -591,47 +878,51 @@ __device__ __forceinline__ double front_value(const RunDesc& rd, const S* base, 
     return __ddiv_rn(__dsub_rn(a, b), __dadd_rn(a, b));
 }
 
+constexpr int kTrackGroup = 256;
+
 template <typename S>
-__global__ void __launch_bounds__(128) k_track(const RunDesc* __restrict__ runs, int parity, LogCtl lc,
-                                               double* __restrict__ zout) {
+__global__ void __launch_bounds__(4 * kTrackGroup) k_track(const RunDesc* __restrict__ runs, int parity, LogCtl lc,
+                                                          double* __restrict__ zout) {
     const RunDesc& rd = runs[blockIdx.x];
     __shared__ double zr[4];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int first[4];
+    const int grp_id = threadIdx.x / kTrackGroup, lt = threadIdx.x % kTrackGroup;
     const bool has = rd.y_bot >= 0 && rd.y_top >= 0 && rd.y_top - rd.y_bot >= 2 && rd.cap_x1 > rd.cap_x0;
+    if (lt == 0) first[grp_id] = 0x7fffffff;
+    __syncthreads();
+    Shift<S> sh;
+    sh.load(rd);
+    const S* base = static_cast<const S*>(rd.buf[parity]);
+    int y = 0;
+    const bool prec = grp_id >= 2;
     if (has) {
-        Shift<S> sh;
-        sh.load(rd);
-        const S* base = static_cast<const S*>(rd.buf[parity]);
         const int H = rd.y_top - rd.y_bot - 1;
-        int y;
-        if (warp == 0) y = (H % 2 == 0) ? rd.y_bot + H / 2 : rd.y_bot + (H + 1) / 2;
-        else if (warp == 1) y = (H % 2 == 0) ? rd.y_bot + H / 2 + 1 : rd.y_bot + (H + 1) / 2;
-        else if (warp == 2) y = rd.y_bot + 1;
+        if (grp_id == 0) y = (H % 2 == 0) ? rd.y_bot + H / 2 : rd.y_bot + (H + 1) / 2;
+        else if (grp_id == 1) y = (H % 2 == 0) ? rd.y_bot + H / 2 + 1 : rd.y_bot + (H + 1) / 2;
+        else if (grp_id == 2) y = rd.y_bot + 1;
         else y = rd.y_top - 1;
-        const bool prec = warp >= 2;
-        int found = -1;
-        for (int x0 = rd.cap_x0; x0 < rd.cap_x1 && found < 0; x0 += 32) {
-            const int x = x0 + lane;
-            bool fail = false;
-            if (x < rd.cap_x1) fail = front_value<S>(rd, base, sh, x, y, prec) < 0.0;
-            const unsigned b = __ballot_sync(0xffffffffu, fail);
-            if (b) found = x0 + __ffs(b) - 1;
-        }
-        if (lane == 0) {
-            double z;
-            if (found < 0) {
-                z = (double)(rd.cap_x1 - rd.cap_x0);
-            } else {
-                const int xp = found == 0 ? rd.nx - 1 : found - 1;
-                const double v = front_value<S>(rd, base, sh, found, y, prec);
-                const double vp = front_value<S>(rd, base, sh, xp, y, prec);
-                if (!(vp >= 0.0)) z = (double)(found - rd.cap_x0);
-                else z = __dadd_rn((double)(found - 1 - rd.cap_x0), __ddiv_rn(vp, __dsub_rn(vp, v)));
+        for (int x = rd.cap_x0 + lt; x < rd.cap_x1; x += kTrackGroup)
+            if (front_value<S>(rd, base, sh, x, y, prec) < 0.0) {
+                atomicMin(&first[grp_id], x);
+                break;
             }
-            zr[warp] = z;
+    }
+    __syncthreads();
+    if (lt == 0) {
+        double z;
+        if (!has) {
+            z = __longlong_as_double(0x7ff8000000000000LL);  // NaN: no channel
+        } else if (first[grp_id] == 0x7fffffff) {
+            z = (double)(rd.cap_x1 - rd.cap_x0);
+        } else {
+            const int found = first[grp_id];
+            const int xp = found == 0 ? rd.nx - 1 : found - 1;
+            const double v = front_value<S>(rd, base, sh, found, y, prec);
+            const double vp = front_value<S>(rd, base, sh, xp, y, prec);
+            if (!(vp >= 0.0)) z = (double)(found - rd.cap_x0);
+            else z = __dadd_rn((double)(found - 1 - rd.cap_x0), __ddiv_rn(vp, __dsub_rn(vp, v)));
         }
-    } else if (lane == 0) {
-        zr[warp] = __longlong_as_double(0x7ff8000000000000LL);  // NaN: no channel
+        zr[grp_id] = z;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -659,31 +950,29 @@ __global__ void __launch_bounds__(128) k_track(const RunDesc* __restrict__ runs,
 }
 
 // ---- deterministic FP64 mass sums -----------------------------------------
-// Pass 1: one CTA per (run, row): thread t sums columns t, t + 256, ... in
-// order, then a fixed shared-memory tree.  Pass 2: one CTA per run sums its
-// rows the same way.  The order never depends on timing, so repeated runs
-// give identical bits.
+// Pass 1: one CTA of kMassThreads per (run, row): thread t sums columns t,
+// t + kMassThreads, ... in order, then a fixed shared-memory tree.  Pass 2:
+// one CTA per run sums its rows the same way.  The order never depends on
+// timing, so repeated runs give identical bits.
+constexpr int kMassThreads = 512;
+
 template <typename S>
-__global__ void __launch_bounds__(256) k_mass_rows(const RunDesc* __restrict__ runs, const int2* __restrict__ rows,
-                                                   int parity, double* __restrict__ partials) {
-    const int2 ry = rows[blockIdx.x];
-    const RunDesc& rd = runs[ry.x];
+__device__ __forceinline__ void mass_row_sum(const RunDesc& rd, const S* base, int y, double* out2) {
     Shift<S> sh;
     sh.load(rd);
     const Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
-    const S* base = static_cast<const S*>(rd.buf[parity]);
     double a = 0.0, b = 0.0;
-    for (int x = threadIdx.x; x < rd.nx; x += 256) {
-        if (geo.solid(x, ry.y)) continue;
-        const long long o = (long long)ry.y * rd.pitch + x;
+    for (int x = threadIdx.x; x < rd.nx; x += kMassThreads) {
+        if (geo.solid(x, y)) continue;
+        const long long o = (long long)y * rd.pitch + x;
         a = __dadd_rn(a, node_density<S>(rd, base, sh, 0, o));
         b = __dadd_rn(b, node_density<S>(rd, base, sh, 1, o));
     }
-    __shared__ double s[2][256];
+    __shared__ double s[2][kMassThreads];
     s[0][threadIdx.x] = a;
     s[1][threadIdx.x] = b;
     __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
+    for (int h = kMassThreads / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) {
             s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
             s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
@@ -691,12 +980,45 @@ __global__ void __launch_bounds__(256) k_mass_rows(const RunDesc* __restrict__ r
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x + 0] = s[0][0];
-        partials[2 * blockIdx.x + 1] = s[1][0];
+        out2[0] = s[0][0];
+        out2[1] = s[1][0];
     }
 }
 
-__global__ void __launch_bounds__(256) k_mass_final(const RunDesc* __restrict__ runs,
+template <typename S>
+__global__ void __launch_bounds__(kMassThreads) k_mass_rows(const RunDesc* __restrict__ runs,
+                                                            const int2* __restrict__ rows, int parity,
+                                                            double* __restrict__ partials) {
+    const int2 ry = rows[blockIdx.x];
+    const RunDesc& rd = runs[ry.x];
+    mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[parity]), ry.y, partials + 2 * blockIdx.x);
+}
+
+// Pass 2 over the rows of one run (shared with the allocation-free variant).
+__device__ __forceinline__ void mass_rows_total(int ny, const double* part, double* out2) {
+    double a = 0.0, b = 0.0;
+    for (int y = threadIdx.x; y < ny; y += kMassThreads) {
+        a = __dadd_rn(a, part[2 * y + 0]);
+        b = __dadd_rn(b, part[2 * y + 1]);
+    }
+    __shared__ double s[2][kMassThreads];
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = kMassThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
+            s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = s[0][0];
+        out2[1] = s[1][0];
+    }
+}
+
+__global__ void __launch_bounds__(kMassThreads) k_mass_final(const RunDesc* __restrict__ runs,
                                                     const double* __restrict__ partials, double* __restrict__ mass,
                                                     LogCtl lc, int write_log, uint32_t* __restrict__ err);
 

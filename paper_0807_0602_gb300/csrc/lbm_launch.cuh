@@ -67,6 +67,33 @@ cudaError_t Launch<S>::step_async(int W, int D, const RunDesc* d_runs, const Til
     }
 }
 
+template <typename S, int W>
+static cudaError_t launch_tma(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, uint32_t* err,
+                              cudaStream_t s) {
+    constexpr size_t smem = TmaGeom<S, W>::smem_bytes();
+    static bool configured = false;   // attribute set once per process and instantiation
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_step_tma<S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_tma<S, W><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_tma(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                uint32_t* err, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: return launch_tma<S, 64>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 128: return launch_tma<S, 128>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 256: return launch_tma<S, 256>(d_runs, d_tiles, ntiles, parity, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename S>
 cudaError_t Launch<S>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s) {
@@ -91,7 +118,7 @@ template <typename S>
 cudaError_t Launch<S>::track(const RunDesc* d_runs, int nruns, int parity, LogCtl lc, double* zout,
                              cudaStream_t s) {
     if (nruns <= 0) return cudaSuccess;
-    k_track<S><<<nruns, 128, 0, s>>>(d_runs, parity, lc, zout);
+    k_track<S><<<nruns, 4 * kTrackGroup, 0, s>>>(d_runs, parity, lc, zout);
     return cudaGetLastError();
 }
 
@@ -100,10 +127,10 @@ cudaError_t Launch<S>::mass(const RunDesc* d_runs, int nruns, const int2* d_rows
                             double* d_partials, double* d_mass, LogCtl lc, int write_log, uint32_t* d_err,
                             cudaStream_t s) {
     if (nruns <= 0) return cudaSuccess;
-    k_mass_rows<S><<<nrows, 256, 0, s>>>(d_runs, d_rows, parity, d_partials);
+    k_mass_rows<S><<<nrows, kMassThreads, 0, s>>>(d_runs, d_rows, parity, d_partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_mass_final<<<nruns, 256, 0, s>>>(d_runs, d_partials, d_mass, lc, write_log, d_err);
+    k_mass_final<<<nruns, kMassThreads, 0, s>>>(d_runs, d_partials, d_mass, lc, write_log, d_err);
     return cudaGetLastError();
 }
 

@@ -26,59 +26,14 @@ double* g_row_sums_addr[kMaxDevices] = {};   // device address of g_row_sums per
 
 // Pass 1: one CTA per row, the same order as k_mass_rows.
 template <typename S>
-__global__ void __launch_bounds__(256) k_rows_noalloc(sc::RunDesc rd, double* __restrict__ part) {
-    const int y = blockIdx.x;
-    sc::Shift<S> sh;
-    sh.load(rd);
-    const sc::Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, nullptr};
-    const S* base = static_cast<const S*>(rd.buf[0]);
-    double a = 0.0, b = 0.0;
-    for (int x = threadIdx.x; x < rd.nx; x += 256) {
-        if (geo.solid(x, y)) continue;
-        const long long o = (long long)y * rd.pitch + x;
-        a = __dadd_rn(a, sc::node_density<S>(rd, base, sh, 0, o));
-        b = __dadd_rn(b, sc::node_density<S>(rd, base, sh, 1, o));
-    }
-    __shared__ double s[2][256];
-    s[0][threadIdx.x] = a;
-    s[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
-            s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        part[2 * y + 0] = s[0][0];
-        part[2 * y + 1] = s[1][0];
-    }
+__global__ void __launch_bounds__(sc::kMassThreads) k_rows_noalloc(sc::RunDesc rd, double* __restrict__ part) {
+    sc::mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[0]), blockIdx.x, part + 2 * blockIdx.x);
 }
 
 // Pass 2: one CTA sums the rows in the same order as k_mass_final.
-__global__ void __launch_bounds__(256) k_final_noalloc(int ny, const double* __restrict__ part,
-                                                       double* __restrict__ mass) {
-    double a = 0.0, b = 0.0;
-    for (int y = threadIdx.x; y < ny; y += 256) {
-        a = __dadd_rn(a, part[2 * y + 0]);
-        b = __dadd_rn(b, part[2 * y + 1]);
-    }
-    __shared__ double s[2][256];
-    s[0][threadIdx.x] = a;
-    s[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            s[0][threadIdx.x] = __dadd_rn(s[0][threadIdx.x], s[0][threadIdx.x + h]);
-            s[1][threadIdx.x] = __dadd_rn(s[1][threadIdx.x], s[1][threadIdx.x + h]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        mass[0] = s[0][0];
-        mass[1] = s[1][0];
-    }
+__global__ void __launch_bounds__(sc::kMassThreads) k_final_noalloc(int ny, const double* __restrict__ part,
+                                                                    double* __restrict__ mass) {
+    sc::mass_rows_total(ny, part, mass);
 }
 
 // Device address of g_row_sums for the current device, looked up once per
@@ -132,11 +87,11 @@ extern "C" int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void
     rd.rho_ref[1] = rho_ref ? rho_ref[1] : 0.0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (precision) {
-        case LBM_F64: k_rows_noalloc<double><<<g->ny, 256, 0, s>>>(rd, part); break;
-        case LBM_F32: k_rows_noalloc<float><<<g->ny, 256, 0, s>>>(rd, part); break;
-        default: k_rows_noalloc<__half><<<g->ny, 256, 0, s>>>(rd, part); break;
+        case LBM_F64: k_rows_noalloc<double><<<g->ny, sc::kMassThreads, 0, s>>>(rd, part); break;
+        case LBM_F32: k_rows_noalloc<float><<<g->ny, sc::kMassThreads, 0, s>>>(rd, part); break;
+        default: k_rows_noalloc<__half><<<g->ny, sc::kMassThreads, 0, s>>>(rd, part); break;
     }
-    k_final_noalloc<<<1, 256, 0, s>>>(g->ny, part, mass);
+    k_final_noalloc<<<1, sc::kMassThreads, 0, s>>>(g->ny, part, mass);
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     return LBM_OK;
 }

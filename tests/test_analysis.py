@@ -1,0 +1,56 @@
+"""Host-side analysis: fits on constructed data and the front ODE against the
+paper's closed form."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0807_0602_gb300 import analysis as A
+
+
+def test_front_ode_reduces_to_eq16_for_equal_fluids():
+    # Eq. 15 with rho_l = rho_g and mu_l = mu_g is z'' = 2 g cos / (rho L H) - z' / t_d,
+    # whose solution from rest is Eq. 16
+    L, H, gamma, ct, rho, mu = 200.0, 40.0, 0.02, math.cos(math.radians(40)), 1.0, 1.0 / 6.0
+    t, z = A.front_ode(20000.0, 1.0, 30.0, 0.0, L, H, gamma, ct, rho, rho, mu, mu)
+    ref = A.front_equal_fluids(t, 30.0, L, H, gamma, ct, rho, mu)
+    assert np.max(np.abs(z - ref)) < 1e-9 * max(1.0, np.abs(ref).max())
+
+
+def test_front_ode_tends_to_the_viscous_law():
+    # late times: inertia negligible, z follows the viscous balance of Eq. 15
+    L, H, gamma, ct = 400.0, 20.0, 0.05, 1.0
+    rl, rg, ml, mg = 1.0, 0.3, 0.5, 0.05
+    t, z = A.front_ode(4e5, 2.0, 10.0, 0.0, L, H, gamma, ct, rl, rg, ml, mg)
+    tv = A.viscous_front_time(z, 10.0, L, H, gamma, ct, ml, mg)
+    late = t > 2e5
+    assert np.max(np.abs(tv[late] - t[late]) / t[late]) < 0.02
+
+
+def test_washburn_and_sqrt_fits_recover_constructed_prefactors():
+    t = np.linspace(0, 1e4, 201)
+    z = np.sqrt(100.0 + 0.37 * t)
+    k, c = A.washburn_slope(t, z)
+    assert k == pytest.approx(0.37, rel=1e-12) and c == pytest.approx(100.0, rel=1e-10)
+    assert A.sqrt_prefactor(t, 0.1 * np.sqrt(t)) == pytest.approx(0.1, rel=1e-12)
+    assert A.washburn_prefactor(0.02, 40, 1.0, 1 / 6) == pytest.approx(0.02 * 40 / 0.5)
+
+
+def test_laplace_fit():
+    inv_r = 1.0 / np.array([10, 13, 16, 20.0])
+    g, c, r2 = A.laplace_gamma(inv_r, 0.02 * inv_r + 1e-5)
+    assert g == pytest.approx(0.02, rel=1e-10) and c == pytest.approx(1e-5, rel=1e-6) and r2 > 0.999999
+
+
+@pytest.mark.parametrize("theta", [30.0, 60.0, 90.0, 120.0])
+def test_droplet_angle_of_a_constructed_cap(theta):
+    # a circular cap of radius 30 meeting the wall y = 0.5 at angle theta
+    ny, nx, R = 96, 160, 30.0
+    yc = 0.5 - R * math.cos(math.radians(theta))
+    ys, xs = np.mgrid[0:ny, 0:nx].astype(float)
+    d = np.hypot(xs - 80.0, ys - yc) - R
+    phi = np.clip(-np.tanh(d / 2.0), -0.99, 0.99)
+    nA, nB = (1 + phi), (1 - phi)
+    nA[0], nB[0] = 0.0, 0.0
+    ang, circ = A.droplet_contact_angle(nA, nB, wall_y=0.5, skip_rows=3)
+    assert ang == pytest.approx(theta, abs=1.0)

@@ -46,10 +46,12 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
-def test_binding_declares_every_lbm_symbol():
-    from paper_0807_0602_gb300 import _lib
-    lbm_names = [n for n in declared_functions() if n.startswith("lbm_")]
-    assert set(lbm_names) <= set(_lib.SIGNATURES)
+def test_binding_declares_every_symbol():
+    from paper_0807_0602_gb300 import _lib, surrogate
+    names = declared_functions()
+    assert set(n for n in names if n.startswith("lbm_")) <= set(_lib.SIGNATURES)
+    assert set(n for n in names if n.startswith("mlp_")) <= set(surrogate.MLP_SIGNATURES)
+    assert set(names) <= set(_lib.SIGNATURES) | set(surrogate.MLP_SIGNATURES)
 
 
 def _geom(nx=16, ny=8):

@@ -133,6 +133,7 @@ def test_results_independent_of_tiling_and_graphs(prec):
               ((128, 100), 7, None)]
     if prec != "f16s":
         scheds += [((128, 16), 0, (1, 4)), ((64, 5), -1, (1, 3)), ((256, 8), 3, (1, 4)), ((64, 40), 0, (1, 4))]
+    scheds += [((128, 16), 0, (2, 4)), ((64, 1), -1, (2, 4)), ((256, 7), 5, (2, 4)), ((64, 37), 0, (2, 4))]
     outs = []
     for tile, chunk, kern in scheds:
         with Lattice(run, precision=prec, tile=tile, graph_chunk=chunk, rho_ref=(1.0, 1.0), kernel=kern) as lat:
@@ -142,6 +143,30 @@ def test_results_independent_of_tiling_and_graphs(prec):
             outs.append(lat.populations())
     for o in outs[1:]:
         assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
+
+
+@pytest.mark.parametrize("name", ["capillary64x18", "odd17x9", "tiny5x4", "wide300x5", "box16x8"])
+@pytest.mark.parametrize("tile", [(64, 3), (128, 16), (256, 40)])
+def test_tma_kernel_fp64_matches_oracle(name, tile):
+    geom, prm, kind = CASES[name]
+    nA, nB = _fields(geom, kind)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(30)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=tile,
+                 kernel=(2, 4)) as lat:
+        lat.step(30)
+        F = lat.populations()
+    assert np.array_equal(F, ref.populations())
+
+
+def test_tma_kernel_rejected_below_four_columns():
+    from paper_0807_0602_gb300 import _lib as L
+    geom, prm, kind = CASES["row3x1"]
+    nA, nB = _fields(geom, kind)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f32") as lat:
+        with pytest.raises(L.LbmError) as e:
+            lat.schedule = (128, 16, 2, 4)
+        assert e.value.code == L.LBM_EINVAL
 
 
 def test_async_kernel_fp64_matches_oracle():
@@ -265,7 +290,7 @@ def test_full_size_capillary_8192x160_first_steps_match_oracle():
         lat.step(3)
         gA, gB = lat.densities()
     assert rel_err(gA, rA, fluid) <= 1e-12 and rel_err(gB, rB, fluid) <= 1e-12
-    for kern in (None, (1, 4)):
+    for kern in (None, (1, 4), (2, 4)):
         with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision="f32", tile=(128, 16),
                      kernel=kern) as lat:
             lat.step(3)
