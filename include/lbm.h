@@ -246,11 +246,16 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  * depth 3 or 4, not available for LBM_F16S; LBM_KERNEL_TMA: source rows
  * streamed into a shared-memory ring by bulk copies (cp.async.bulk with
  * mbarrier completion), all precisions, every run needs nx >= 4; depth is
- * ignored).  Results do not depend on the schedule.  lbm_set_schedule
+ * ignored; LBM_KERNEL_PIPELINED: register pull with the loads of the row
+ * after next in flight during the collision, all precisions).  Results do
+ * not depend on the schedule.  lbm_set_schedule
  * returns LBM_EINVAL for an unsupported combination. */
 #define LBM_KERNEL_REGISTER 0
 #define LBM_KERNEL_ASYNC 1
 #define LBM_KERNEL_TMA 2
+#define LBM_KERNEL_PIPELINED 3   /* register pull, the next row's loads issued before the collision */
+#define LBM_KERNEL_SPLIT 4       /* one thread per species and node (2 tile_w threads per CTA) */
+#define LBM_KERNEL_PREFETCH 5    /* register pull, rows streamed into L2 ahead by bulk prefetches */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 

@@ -43,7 +43,10 @@ struct lbm_s {
     size_t d_tiles_cap = 0;
     std::vector<int> tile_begin, tile_count;
     int tile_w = 128, tile_h = 16;
-    int kvar = 0, depth = 4;       // step kernel: 0 register pull, 1 cp.async stages of depth D, 2 TMA ring
+    int kvar = 0, depth = 4;       // step kernel: 0 register pull, 1 cp.async stages of depth D, 2 TMA ring,
+                                   // 3 register pull with the next row's loads in flight,
+                                   // 4 species split over two threads per node,
+                                   // 5 register pull with bulk L2 prefetch of rows ahead
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -116,9 +119,13 @@ cudaError_t dispatch(int precision, F&& f) {
 
 bool finite(double v) { return std::isfinite(v); }
 
+int round_pitch(int nx);
+
 int validate_geometry(const lbm_geometry& g) {
     if (g.nx < 1 || g.ny < 1) return LBM_EINVAL;
     if ((long long)g.nx * g.ny > (1LL << 31) / 2) return LBM_EINVAL;
+    // element indices within one buffer are 32-bit in the step kernels
+    if (18LL * g.ny * round_pitch(g.nx) >= (1LL << 31)) return LBM_EINVAL;
     if (g.cap_x0 < 0 || g.cap_x1 < g.cap_x0 || g.cap_x1 > g.nx) return LBM_EINVAL;
     if (g.y_bot < -1 || g.y_bot >= g.ny || g.y_top < -1 || g.y_top >= g.ny) return LBM_EINVAL;
     if (g.init_kind < LBM_INIT_SLAB || g.init_kind > LBM_INIT_FIELDS) return LBM_EINVAL;
@@ -203,12 +210,18 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     if (h->kvar == 2)
         return dispatch(h->precision,
                         [&](auto L) { return L.step_tma(W, h->d_runs, h->d_tiles, nt, parity, h->d_err, s); });
+    if (h->kvar == 3)
+        return dispatch(h->precision, [&](auto L) { return L.step_pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 4)
+        return dispatch(h->precision, [&](auto L) { return L.step_split(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 5)
+        return dispatch(h->precision, [&](auto L) { return L.step_l2pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
     return dispatch(h->precision, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
     if (W != 64 && W != 128 && W != 256) return false;
-    if (R < 1 || kvar < 0 || kvar > 2) return false;
+    if (R < 1 || kvar < 0 || kvar > 5) return false;
     if (kvar == 1 && (h->precision == LBM_F16S || (depth != 3 && depth != 4))) return false;
     if (kvar == 2) {
         // the TMA windows rely on two ghost columns each side: nx >= 4
@@ -306,6 +319,9 @@ int autotune(lbm_t* h, int64_t* n) {
     for (int W : {64, 128, 256})
         for (int R : Rs) {
             cands.push_back({W, R, 0, 4});
+            cands.push_back({W, R, 3, 4});
+            cands.push_back({W, R, 4, 4});
+            cands.push_back({W, R, 5, 4});
             if (schedule_ok(h, W, R, 2, 4)) cands.push_back({W, R, 2, 4});
             if (W < 256 && schedule_ok(h, W, R, 1, 4)) cands.push_back({W, R, 1, 4});
         }

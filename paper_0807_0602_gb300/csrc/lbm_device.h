@@ -61,6 +61,12 @@ struct Launch {
                                   cudaStream_t s);
     static cudaError_t step_tma(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                 uint32_t* err, cudaStream_t s);
+    static cudaError_t step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                               cudaStream_t s);
+    static cudaError_t step_split(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s);
+    static cudaError_t step_l2pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
     static cudaError_t densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA,

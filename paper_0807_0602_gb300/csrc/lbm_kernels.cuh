@@ -63,6 +63,10 @@ template <> struct Ar<double> {
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
 };
+// FP64 evaluates the canonical order; FP32 may use cheaper equivalent forms.
+template <typename C> constexpr bool kCanonical = true;
+template <> constexpr bool kCanonical<float> = false;
+
 template <> struct Ar<float> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
@@ -143,24 +147,40 @@ __device__ __forceinline__ unsigned nbr_solid(const Geo& g, int xm, int xc, int 
 
 // Pull of one node (step 1) and its densities (step 2).
 template <typename S>
-__device__ __forceinline__ void pull_node(const S* __restrict__ src, long long plane, long long own,
-                                          long long oxm, long long oxp, long long orm, long long orp,
-                                          long long orm_xm, long long orm_xp, long long orp_xm,
-                                          long long orp_xp, unsigned sm, const Shift<S>& sh,
+__device__ __forceinline__ void pull_node(const S* __restrict__ src, unsigned plane, unsigned own,
+                                          unsigned oxm, unsigned oxp, unsigned orm, unsigned orp,
+                                          unsigned orm_xm, unsigned orm_xp, unsigned orp_xm,
+                                          unsigned orp_xp, unsigned sm, const Shift<S>& sh,
                                           typename Prec<S>::C (&f)[2][9]) {
     // source of direction i is x - c_i; offsets: own row/col combos
+    if (sm == 0) {   // no solid neighbour (almost every node): no bounce-back selects
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const S* p = src + (unsigned)(k * 9) * plane;
+            f[k][0] = dec(ldg(p + own), sh.v[k][0]);
+            f[k][1] = dec(ldg(p + (1 * plane + oxm)), sh.v[k][1]);
+            f[k][2] = dec(ldg(p + (2 * plane + orm)), sh.v[k][1]);
+            f[k][3] = dec(ldg(p + (3 * plane + oxp)), sh.v[k][1]);
+            f[k][4] = dec(ldg(p + (4 * plane + orp)), sh.v[k][1]);
+            f[k][5] = dec(ldg(p + (5 * plane + orm_xm)), sh.v[k][2]);
+            f[k][6] = dec(ldg(p + (6 * plane + orm_xp)), sh.v[k][2]);
+            f[k][7] = dec(ldg(p + (7 * plane + orp_xp)), sh.v[k][2]);
+            f[k][8] = dec(ldg(p + (8 * plane + orp_xm)), sh.v[k][2]);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const S* p = src + (long long)k * 9 * plane;
+        const S* p = src + (unsigned)(k * 9) * plane;
         f[k][0] = dec(ldg(p + own), sh.v[k][0]);
-        f[k][1] = dec(ldg(SOL(sm, 0, -1) ? p + 3 * plane + own : p + 1 * plane + oxm), sh.v[k][1]);
-        f[k][2] = dec(ldg(SOL(sm, -1, 0) ? p + 4 * plane + own : p + 2 * plane + orm), sh.v[k][1]);
-        f[k][3] = dec(ldg(SOL(sm, 0, 1) ? p + 1 * plane + own : p + 3 * plane + oxp), sh.v[k][1]);
-        f[k][4] = dec(ldg(SOL(sm, 1, 0) ? p + 2 * plane + own : p + 4 * plane + orp), sh.v[k][1]);
-        f[k][5] = dec(ldg(SOL(sm, -1, -1) ? p + 7 * plane + own : p + 5 * plane + orm_xm), sh.v[k][2]);
-        f[k][6] = dec(ldg(SOL(sm, -1, 1) ? p + 8 * plane + own : p + 6 * plane + orm_xp), sh.v[k][2]);
-        f[k][7] = dec(ldg(SOL(sm, 1, 1) ? p + 5 * plane + own : p + 7 * plane + orp_xp), sh.v[k][2]);
-        f[k][8] = dec(ldg(SOL(sm, 1, -1) ? p + 6 * plane + own : p + 8 * plane + orp_xm), sh.v[k][2]);
+        f[k][1] = dec(ldg(SOL(sm, 0, -1) ? p + (3 * plane + own) : p + (1 * plane + oxm)), sh.v[k][1]);
+        f[k][2] = dec(ldg(SOL(sm, -1, 0) ? p + (4 * plane + own) : p + (2 * plane + orm)), sh.v[k][1]);
+        f[k][3] = dec(ldg(SOL(sm, 0, 1) ? p + (1 * plane + own) : p + (3 * plane + oxp)), sh.v[k][1]);
+        f[k][4] = dec(ldg(SOL(sm, 1, 0) ? p + (2 * plane + own) : p + (4 * plane + orp)), sh.v[k][1]);
+        f[k][5] = dec(ldg(SOL(sm, -1, -1) ? p + (7 * plane + own) : p + (5 * plane + orm_xm)), sh.v[k][2]);
+        f[k][6] = dec(ldg(SOL(sm, -1, 1) ? p + (8 * plane + own) : p + (6 * plane + orm_xp)), sh.v[k][2]);
+        f[k][7] = dec(ldg(SOL(sm, 1, 1) ? p + (5 * plane + own) : p + (7 * plane + orp_xp)), sh.v[k][2]);
+        f[k][8] = dec(ldg(SOL(sm, 1, -1) ? p + (6 * plane + own) : p + (8 * plane + orp_xm)), sh.v[k][2]);
     }
 }
 
@@ -175,9 +195,9 @@ __device__ __forceinline__ C dens9(const C (&f)[9]) {
 struct RowIdx {
     int rm, rw, rp;
 };
+// Rows of a march lie in [-1, ny]: one conditional wrap, no division.
 __device__ __forceinline__ RowIdx rows_of(int r, int ny) {
-    int rw = r % ny;
-    if (rw < 0) rw += ny;
+    const int rw = r < 0 ? r + ny : (r >= ny ? r - ny : r);
     RowIdx q;
     q.rw = rw;
     q.rm = rw == 0 ? ny - 1 : rw - 1;
@@ -219,10 +239,10 @@ __device__ __forceinline__ int ghost_l(int x, int nx) { return x >= nx - 2 ? -nx
 // periodic images at x = nx, nx + 1 and x = -2, -1 (ghost columns), so that
 // every source row a later step reads is one contiguous window; gr / gl give
 // the offsets of those images from the node (0 = none).
-template <typename S, int W, int MODE>
+template <typename S, int W, int MODE, bool GH = true>
 __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
                                              const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
-                                             S* __restrict__ dst, long long plane, long long o, MomOut mo,
+                                             S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
                                              long long mo_idx, int gr = 0, int gl = 0) {
     using C = typename Prec<S>::C;
     using Wc = Wt<C>;
@@ -278,8 +298,17 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
     }
     // common velocity (Eq. 8) and shifted equilibrium velocities (Eq. 7)
     const C den = A::fma(n[0], cx.itau[0], A::mul(n[1], cx.itau[1]));
-    const C Ux = A::div(A::fma(jx[0], cx.itau[0], A::mul(jx[1], cx.itau[1])), den);
-    const C Uy = A::div(A::fma(jy[0], cx.itau[0], A::mul(jy[1], cx.itau[1])), den);
+    const C numx = A::fma(jx[0], cx.itau[0], A::mul(jx[1], cx.itau[1]));
+    const C numy = A::fma(jy[0], cx.itau[0], A::mul(jy[1], cx.itau[1]));
+    C Ux, Uy;
+    if constexpr (kCanonical<C>) {
+        Ux = A::div(numx, den);
+        Uy = A::div(numy, den);
+    } else {
+        const C rden = __frcp_rn(den);   // one reciprocal for both components
+        Ux = A::mul(numx, rden);
+        Uy = A::mul(numy, rden);
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const C ux = A::fma(cx.tau[k], ax[k], Ux);
@@ -287,22 +316,64 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
         const C usq = A::fma(ux, ux, A::mul(uy, uy));
         const C b = A::mul(C(1.5), usq);
         const C wn0 = A::mul(Wc::w0, n[k]), wn1 = A::mul(Wc::w1, n[k]), wn5 = A::mul(Wc::w5, n[k]);
-        const C cu[9] = {C(0), ux, uy, -ux, -uy, A::add(ux, uy), A::add(-ux, uy), A::sub(-ux, uy), A::sub(ux, uy)};
-        S* d = dst + (long long)k * 9 * plane + o;
+        C fnew[9];
+        if constexpr (kCanonical<C>) {
+            const C cu[9] = {C(0), ux, uy, -ux, -uy, A::add(ux, uy), A::add(-ux, uy), A::sub(-ux, uy), A::sub(ux, uy)};
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
-            const C c = cu[i];
-            // Eqs. 3-5: wn (((1 + 3 c) + 4.5 (c c)) - b)
-            const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
-            const C f = fc[k][i];
-            S* p = d + (long long)i * plane;
-            const C fnew = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
-            enc(p, fnew, cx.sh.v[k][grp(i)]);
-            if (gr) enc(p + gr, fnew, cx.sh.v[k][grp(i)]);
-            if (gl) enc(p + gl, fnew, cx.sh.v[k][grp(i)]);
+            for (int i = 0; i < 9; ++i) {
+                const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
+                const C c = cu[i];
+                // Eqs. 3-5: wn (((1 + 3 c) + 4.5 (c c)) - b)
+                const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
+                const C f = fc[k][i];
+                fnew[i] = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
+            }
+        } else {
+            // Eqs. 3-5 by opposite pairs: feq(+-c) = wn (1 + 4.5 c^2 - b) +- 3 wn c;
+            // Eq. 2 as f (1 - 1/tau) + feq / tau
+            const C om = C(1) - cx.itau[k], it = cx.itau[k];
+            const C base = C(1) - b;
+            const C cp[4] = {ux, uy, A::add(ux, uy), A::sub(uy, ux)};
+            const int ia[4] = {1, 2, 5, 6}, ib[4] = {3, 4, 7, 8};
+            C moving = C(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const C wn = q < 2 ? wn1 : wn5;
+                const C c = cp[q];
+                const C sy = A::mul(wn, A::fma(C(4.5), A::mul(c, c), base));
+                const C an = A::mul(A::mul(C(3), wn), c);
+                fnew[ia[q]] = A::fma(A::add(sy, an), it, A::mul(fc[k][ia[q]], om));
+                fnew[ib[q]] = A::fma(A::sub(sy, an), it, A::mul(fc[k][ib[q]], om));
+                moving = A::add(moving, A::add(fnew[ia[q]], fnew[ib[q]]));
+            }
+            // the collision conserves n_k: the rest population takes what the
+            // moving ones leave, so FP32 rounding does not bias the mass
+            fnew[0] = A::sub(n[k], moving);
+        }
+        S* d = dst + ((unsigned)(k * 9) * plane + o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) enc(d + (unsigned)i * plane, fnew[i], cx.sh.v[k][grp(i)]);
+        if (GH) {   // ghost images of the edge columns (rare)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S* p = d + (unsigned)i * plane;
+                if (gr) enc(p + gr, fnew[i], cx.sh.v[k][grp(i)]);
+                if (gl) enc(p + gl, fnew[i], cx.sh.v[k][grp(i)]);
+            }
         }
     }
+}
+
+// Dispatch: the ghost-writing variant only for the edge columns.
+template <typename S, int W, int MODE>
+__device__ __forceinline__ void collide_any(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+                                            const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
+                                            S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
+                                            long long mo_idx, int gr, int gl) {
+    if (gr | gl)
+        collide_node<S, W, MODE, true>(cx, fc, m, sd, s_m, s_0, s_p, t, dst, plane, o, mo, mo_idx, gr, gl);
+    else
+        collide_node<S, W, MODE, false>(cx, fc, m, sd, s_m, s_0, s_p, t, dst, plane, o, mo, mo_idx, 0, 0);
 }
 
 // Column bookkeeping of a strip: thread t <-> column x0 - 1 + t (wrapped).
@@ -325,9 +396,39 @@ struct StripCols {
 // MODE 0: one time step (read buf[parity], write buf[parity ^ 1]).
 // MODE 1: moments of the step from buf[parity] (whole-fluid velocity), no write.
 // Pulled populations travel through registers (plain loads).
-template <typename S, int W, int MODE>
-__global__ void __launch_bounds__(W) k_step(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
-                                            int parity, MomOut mo) {
+// Occupancy target of the FP32-arithmetic register kernel: about 640
+// threads per SM (96 registers); FP64 keeps the compiler's choice.
+template <typename S, int W>
+constexpr int kMinBlocks = (sizeof(typename Prec<S>::C) == 8 || W >= 640) ? 1 : 640 / W;
+
+// Bulk prefetch of the strip's source rows from HBM into L2: lane q < 18 of
+// warp 0 streams population plane q of a row, columns [x0 - 2, x0 + W - 1]
+// rounded out to 16 bytes (contiguous thanks to the ghost columns).
+template <typename S, int W>
+struct RowPrefetch {
+    const S* base = nullptr;   // plane q, row 0, first column of the window
+    unsigned bytes = 0;
+    __device__ __forceinline__ void init(const S* src, unsigned plane, int pitch, int x0) {
+        constexpr int per16 = 16 / (int)sizeof(S);
+        const int c0 = (x0 - 2 >= 0 ? x0 - 2 : -per16) & ~(per16 - 1);
+        int c1 = min(x0 + W, pitch - LBM_COL0);
+        c1 = min((c1 + per16 - 1) & ~(per16 - 1), pitch - LBM_COL0);
+        if (threadIdx.x < 18 && c1 > c0) {
+            base = src + (unsigned)threadIdx.x * plane + c0;
+            bytes = (unsigned)((c1 - c0) * (int)sizeof(S));
+        }
+    }
+    __device__ __forceinline__ void row(int w, int pitch) const {
+        if (bytes)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(base + (unsigned)(w * pitch)),
+                         "r"(bytes)
+                         : "memory");
+    }
+};
+
+template <typename S, int W, int MODE, bool L2PF = false>
+__global__ void __launch_bounds__(W, (kMinBlocks<S, W>)) k_step(const RunDesc* __restrict__ runs,
+                                                              const Tile* __restrict__ tiles, int parity, MomOut mo) {
     using C = typename Prec<S>::C;
     __shared__ C sd[4][2][W];
 
@@ -353,8 +454,8 @@ __global__ void __launch_bounds__(W) k_step(const RunDesc* __restrict__ runs, co
         if (sc.dcol) {
             smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
             if (!SOL(smask, 0, 0)) {
-                const long long bw = (long long)q.rw * pitch, bm = (long long)q.rm * pitch,
-                                bp = (long long)q.rp * pitch;
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
                 pull_node<S>(src, plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc, bm + sc.xm,
                              bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, cx.sh, f);
                 nA = dens9(f[0]);
@@ -365,29 +466,369 @@ __global__ void __launch_bounds__(W) k_step(const RunDesc* __restrict__ runs, co
         sd[slot][1][t] = nB;
     };
 
-    const int y0 = tl.y0, y1 = tl.y1;
-    pull_row(y0 - 1, fn, smn, 0);
-    pull_row(y0, fc, smc, 1);
-    for (int r = y0; r < y1; ++r) {
-        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
-        pull_row(r + 1, fn, smn, s_p);
+    // row r: pull row r + 1 into (fnext, snext), then collide row r from
+    // (fcur, scur); the march alternates the two register sets so that no
+    // copy is needed between rows
+    RowPrefetch<S, W> pf;
+    if (L2PF) pf.init(src, (unsigned)plane, pitch, tl.x0);
+    auto prefetch = [&](int srow) {   // source row srow in [-2, ny + 5]
+        int w = srow < 0 ? srow + ny : srow;
+        w = w >= ny ? w - ny : w;
+        w = w >= ny ? w % ny : w;     // only for ny < 6
+        pf.row(w, pitch);
+    };
+    auto row = [&](int r, C (&fcur)[2][9], unsigned scur, C (&fnext)[2][9], unsigned& snext) {
+        const int s_m = (r - tl.y0) & 3, s_0 = (r - tl.y0 + 1) & 3, s_p = (r - tl.y0 + 2) & 3;
+        if (L2PF && r + 4 <= tl.y1 + 1) prefetch(r + 4);   // source row needed three rows later
+        pull_row(r + 1, fnext, snext, s_p);
         __syncthreads();
         if (sc.coll) {
             const RowIdx q = rows_of(r, ny);
-            if (!SOL(smc, 0, 0))
-                collide_node<S, W, MODE>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane,
-                                         (long long)q.rw * pitch + sc.xc, mo, (long long)q.rw * mo.nx + sc.xc,
+            if (!SOL(scur, 0, 0))
+                collide_any<S, W, MODE>(cx, fcur, scur, sd, s_m, s_0, s_p, t, dst, plane,
+                                         (unsigned)(q.rw * pitch + sc.xc), mo, (long long)q.rw * mo.nx + sc.xc,
                                          ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
             else if (MODE == 1) {
                 mo.ux[(long long)q.rw * mo.nx + sc.xc] = 0.0;
                 mo.uy[(long long)q.rw * mo.nx + sc.xc] = 0.0;
             }
         }
+    };
+    const int y0 = tl.y0, y1 = tl.y1;
+    if (L2PF)
+        for (int sr = y0 - 2; sr <= min(y0 + 3, y1 + 1); ++sr) prefetch(sr);
+    pull_row(y0 - 1, fn, smn, 0);
+    pull_row(y0, fc, smc, 1);
+    int r = y0;
+    for (; r + 1 < y1; r += 2) {
+        row(r, fc, smc, fn, smn);
+        row(r + 1, fn, smn, fc, smc);
+    }
+    if (r < y1) row(r, fc, smc, fn, smn);
+}
+
+// ---- species-split variant -----------------------------------------------------
+// A CTA of 2W threads: thread (k, c) = (threadIdx.x / W, threadIdx.x % W)
+// owns species k of strip column c (same strip/row march as k_step).  Each
+// thread pulls 9 populations instead of 18, so it needs about half the
+// registers and twice as many warps fit on an SM.  The species meet through
+// shared memory: the density ring (both species, as in k_step) and a
+// double-buffered row of momenta j_k for the common velocity.  One
+// __syncthreads per row.  The arithmetic per node is that of collide_node,
+// done by the thread of each species for its own populations.
+template <typename S, int W, bool GH>
+__device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, const typename Prec<S>::C (&f)[9],
+                                                unsigned m, const typename Prec<S>::C (*sd)[2][W],
+                                                const typename Prec<S>::C (*jb)[W], int s_m, int s_0, int s_p, int c,
+                                                S* __restrict__ dst, unsigned plane, unsigned o, int gr, int gl) {
+    using C = typename Prec<S>::C;
+    using Wc = Wt<C>;
+    using A = Ar<C>;
+    const int kb = 1 - k;
+    const C nA = sd[s_0][0][c], nB = sd[s_0][1][c];
+    const C jxA = jb[0][c], jyA = jb[1][c], jxB = jb[2][c], jyB = jb[3][c];
+    C Wx = C(0), Wy = C(0);
+    if (m) {
+        if (SOL(m, 0, 1)) Wx = A::add(Wx, Wc::w1);
+        if (SOL(m, 1, 0)) Wy = A::add(Wy, Wc::w1);
+        if (SOL(m, 0, -1)) Wx = A::sub(Wx, Wc::w1);
+        if (SOL(m, -1, 0)) Wy = A::sub(Wy, Wc::w1);
+        if (SOL(m, 1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }
+        if (SOL(m, 1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }
+        if (SOL(m, -1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); }
+        if (SOL(m, -1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); }
+    }
+    const C n1 = sd[s_0][kb][c + 1], n2 = sd[s_p][kb][c], n3 = sd[s_0][kb][c - 1], n4 = sd[s_m][kb][c],
+            n5 = sd[s_p][kb][c + 1], n6 = sd[s_p][kb][c - 1], n7 = sd[s_m][kb][c - 1], n8 = sd[s_m][kb][c + 1];
+    C Sx = A::fma(-Wc::w1, n3, A::mul(Wc::w1, n1));
+    Sx = A::fma(Wc::w5, n5, Sx);
+    Sx = A::fma(-Wc::w5, n6, Sx);
+    Sx = A::fma(-Wc::w5, n7, Sx);
+    Sx = A::fma(Wc::w5, n8, Sx);
+    C Sy = A::fma(-Wc::w1, n4, A::mul(Wc::w1, n2));
+    Sy = A::fma(Wc::w5, n5, Sy);
+    Sy = A::fma(Wc::w5, n6, Sy);
+    Sy = A::fma(-Wc::w5, n7, Sy);
+    Sy = A::fma(-Wc::w5, n8, Sy);
+    const C ax = A::add(A::sub(-A::mul(cx.G, Sx), A::mul(cx.Gw[k], Wx)), cx.gx);
+    const C ay = A::add(A::sub(-A::mul(cx.G, Sy), A::mul(cx.Gw[k], Wy)), cx.gy);
+    const C den = A::fma(nA, cx.itau[0], A::mul(nB, cx.itau[1]));
+    const C numx = A::fma(jxA, cx.itau[0], A::mul(jxB, cx.itau[1]));
+    const C numy = A::fma(jyA, cx.itau[0], A::mul(jyB, cx.itau[1]));
+    C Ux, Uy;
+    if constexpr (kCanonical<C>) {
+        Ux = A::div(numx, den);
+        Uy = A::div(numy, den);
+    } else {
+        const C rden = __frcp_rn(den);
+        Ux = A::mul(numx, rden);
+        Uy = A::mul(numy, rden);
+    }
+    const C n = k == 0 ? nA : nB;
+    const C ux = A::fma(cx.tau[k], ax, Ux);
+    const C uy = A::fma(cx.tau[k], ay, Uy);
+    const C usq = A::fma(ux, ux, A::mul(uy, uy));
+    const C b = A::mul(C(1.5), usq);
+    const C wn0 = A::mul(Wc::w0, n), wn1 = A::mul(Wc::w1, n), wn5 = A::mul(Wc::w5, n);
+    C fnew[9];
+    if constexpr (kCanonical<C>) {
+        const C cu[9] = {C(0), ux, uy, -ux, -uy, A::add(ux, uy), A::add(-ux, uy), A::sub(-ux, uy), A::sub(ux, uy)};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
+            const C cc = cu[i];
+            const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(cc, cc), A::fma(C(3), cc, C(1))), b));
+            fnew[i] = A::fma(-A::sub(f[i], feq), cx.itau[k], f[i]);
+        }
+    } else {
+        const C om = C(1) - cx.itau[k], it = cx.itau[k];
+        const C base = C(1) - b;
+        const C cp[4] = {ux, uy, A::add(ux, uy), A::sub(uy, ux)};
+        const int ia[4] = {1, 2, 5, 6}, ib[4] = {3, 4, 7, 8};
+        C moving = C(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C wn = q < 2 ? wn1 : wn5;
+            const C cc = cp[q];
+            const C sy = A::mul(wn, A::fma(C(4.5), A::mul(cc, cc), base));
+            const C an = A::mul(A::mul(C(3), wn), cc);
+            fnew[ia[q]] = A::fma(A::add(sy, an), it, A::mul(f[ia[q]], om));
+            fnew[ib[q]] = A::fma(A::sub(sy, an), it, A::mul(f[ib[q]], om));
+            moving = A::add(moving, A::add(fnew[ia[q]], fnew[ib[q]]));
+        }
+        fnew[0] = A::sub(n, moving);   // exact per-node mass balance
+    }
+    S* d = dst + ((unsigned)(k * 9) * plane + o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) enc(d + (unsigned)i * plane, fnew[i], cx.sh.v[k][grp(i)]);
+    if (GH) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            S* p = d + (unsigned)i * plane;
+            if (gr) enc(p + gr, fnew[i], cx.sh.v[k][grp(i)]);
+            if (gl) enc(p + gl, fnew[i], cx.sh.v[k][grp(i)]);
+        }
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ void pull_species(const S* __restrict__ p, unsigned plane, unsigned own, unsigned oxm,
+                                             unsigned oxp, unsigned orm, unsigned orp, unsigned orm_xm,
+                                             unsigned orm_xp, unsigned orp_xm, unsigned orp_xp, unsigned sm,
+                                             typename Prec<S>::C sh0, typename Prec<S>::C sh1,
+                                             typename Prec<S>::C sh2, typename Prec<S>::C (&f)[9]) {
+    if (sm == 0) {
+        f[0] = dec(ldg(p + own), sh0);
+        f[1] = dec(ldg(p + (1 * plane + oxm)), sh1);
+        f[2] = dec(ldg(p + (2 * plane + orm)), sh1);
+        f[3] = dec(ldg(p + (3 * plane + oxp)), sh1);
+        f[4] = dec(ldg(p + (4 * plane + orp)), sh1);
+        f[5] = dec(ldg(p + (5 * plane + orm_xm)), sh2);
+        f[6] = dec(ldg(p + (6 * plane + orm_xp)), sh2);
+        f[7] = dec(ldg(p + (7 * plane + orp_xp)), sh2);
+        f[8] = dec(ldg(p + (8 * plane + orp_xm)), sh2);
+        return;
+    }
+    f[0] = dec(ldg(p + own), sh0);
+    f[1] = dec(ldg(SOL(sm, 0, -1) ? p + (3 * plane + own) : p + (1 * plane + oxm)), sh1);
+    f[2] = dec(ldg(SOL(sm, -1, 0) ? p + (4 * plane + own) : p + (2 * plane + orm)), sh1);
+    f[3] = dec(ldg(SOL(sm, 0, 1) ? p + (1 * plane + own) : p + (3 * plane + oxp)), sh1);
+    f[4] = dec(ldg(SOL(sm, 1, 0) ? p + (2 * plane + own) : p + (4 * plane + orp)), sh1);
+    f[5] = dec(ldg(SOL(sm, -1, -1) ? p + (7 * plane + own) : p + (5 * plane + orm_xm)), sh2);
+    f[6] = dec(ldg(SOL(sm, -1, 1) ? p + (8 * plane + own) : p + (6 * plane + orm_xp)), sh2);
+    f[7] = dec(ldg(SOL(sm, 1, 1) ? p + (5 * plane + own) : p + (7 * plane + orp_xp)), sh2);
+    f[8] = dec(ldg(SOL(sm, 1, -1) ? p + (6 * plane + own) : p + (8 * plane + orp_xm)), sh2);
+}
+
+template <typename S, int W>
+constexpr int kSplitMinBlocks = (sizeof(typename Prec<S>::C) == 8 || 2 * W >= 1024) ? 1 : 1024 / (2 * W);
+
+template <typename S, int W>
+__global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(const RunDesc* __restrict__ runs,
+                                                                              const Tile* __restrict__ tiles,
+                                                                              int parity) {
+    using C = typename Prec<S>::C;
+    using A = Ar<C>;
+    __shared__ C sd[4][2][W];
+    __shared__ C jb[2][4][W];   // [row parity][jxA, jyA, jxB, jyB][column]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const int k = threadIdx.x / W, c = threadIdx.x % W;
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]) + (unsigned)(k * 9) * (unsigned)plane;
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const C sh0 = cx.sh.v[k][0], sh1 = cx.sh.v[k][1], sh2 = cx.sh.v[k][2];
+    const StripCols sc(tl.x0, nx, W, c);
+
+    auto pull_row = [&](int r, C (&f)[9], unsigned& smask, int slot) {
+        const RowIdx q = rows_of(r, ny);
+        C nk = C(0);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
+                pull_species<S>(src, plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc, bm + sc.xm,
+                                bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, sh0, sh1, sh2, f);
+                nk = dens9(f);
+            }
+        }
+        sd[slot][k][c] = nk;
+    };
+
+    const int y0 = tl.y0, y1 = tl.y1;
+    C fc[9], fn[9];
+    unsigned smc = 0, smn = 0;
+    pull_row(y0 - 1, fn, smn, 0);
+    pull_row(y0, fc, smc, 1);
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        pull_row(r + 1, fn, smn, s_p);
+        // momenta of this species at row r for the common velocity
+        C (*j)[W] = jb[r & 1];
+        if (sc.coll && !SOL(smc, 0, 0)) {
+            j[2 * k][c] = A::add(A::sub(A::sub(A::add(A::sub(fc[1], fc[3]), fc[5]), fc[6]), fc[7]), fc[8]);
+            j[2 * k + 1][c] = A::sub(A::sub(A::add(A::add(A::sub(fc[2], fc[4]), fc[5]), fc[6]), fc[7]), fc[8]);
+        }
+        __syncthreads();
+        if (sc.coll && !SOL(smc, 0, 0)) {
+            const RowIdx q = rows_of(r, ny);
+            const int gr = ghost_r(sc.xc, nx), gl = ghost_l(sc.xc, nx);
+            const unsigned o = (unsigned)(q.rw * pitch + sc.xc);
+            if (gr | gl)
+                collide_species<S, W, true>(cx, k, fc, smc, sd, j, s_m, s_0, s_p, c, dst, plane, o, gr, gl);
+            else
+                collide_species<S, W, false>(cx, k, fc, smc, sd, j, s_m, s_0, s_p, c, dst, plane, o, 0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fc[i] = fn[i];
+        smc = smn;
+    }
+}
+
+// ---- software-pipelined register variant ------------------------------------
+// k_step with the loads of row r + 2 issued (into raw registers) before row
+// r + 1 is decoded and row r collided: each row's HBM latency overlaps a
+// full row of arithmetic instead of stalling it.  Same column/row march,
+// same collision, same bits.
+template <typename S>
+__device__ __forceinline__ void issue_pull(const S* __restrict__ src, unsigned plane, unsigned own, unsigned oxm,
+                                           unsigned oxp, unsigned orm, unsigned orp, unsigned orm_xm,
+                                           unsigned orm_xp, unsigned orp_xm, unsigned orp_xp, unsigned sm,
+                                           S (&raw)[18]) {
+    if (sm == 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const S* p = src + (unsigned)(k * 9) * plane;
+            S* r = raw + k * 9;
+            r[0] = ldg(p + own);
+            r[1] = ldg(p + (1 * plane + oxm));
+            r[2] = ldg(p + (2 * plane + orm));
+            r[3] = ldg(p + (3 * plane + oxp));
+            r[4] = ldg(p + (4 * plane + orp));
+            r[5] = ldg(p + (5 * plane + orm_xm));
+            r[6] = ldg(p + (6 * plane + orm_xp));
+            r[7] = ldg(p + (7 * plane + orp_xp));
+            r[8] = ldg(p + (8 * plane + orp_xm));
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const S* p = src + (unsigned)(k * 9) * plane;
+        S* r = raw + k * 9;
+        r[0] = ldg(p + own);
+        r[1] = ldg(SOL(sm, 0, -1) ? p + (3 * plane + own) : p + (1 * plane + oxm));
+        r[2] = ldg(SOL(sm, -1, 0) ? p + (4 * plane + own) : p + (2 * plane + orm));
+        r[3] = ldg(SOL(sm, 0, 1) ? p + (1 * plane + own) : p + (3 * plane + oxp));
+        r[4] = ldg(SOL(sm, 1, 0) ? p + (2 * plane + own) : p + (4 * plane + orp));
+        r[5] = ldg(SOL(sm, -1, -1) ? p + (7 * plane + own) : p + (5 * plane + orm_xm));
+        r[6] = ldg(SOL(sm, -1, 1) ? p + (8 * plane + own) : p + (6 * plane + orm_xp));
+        r[7] = ldg(SOL(sm, 1, 1) ? p + (5 * plane + own) : p + (7 * plane + orp_xp));
+        r[8] = ldg(SOL(sm, 1, -1) ? p + (6 * plane + own) : p + (8 * plane + orp_xm));
+    }
+}
+
+template <typename S, int W>
+__global__ void __launch_bounds__(W) k_step_pf(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
+                                               int parity) {
+    using C = typename Prec<S>::C;
+    __shared__ C sd[4][2][W];
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const StripCols sc(tl.x0, nx, W, t);
+
+    // issue the loads of row p into raw; smask = solid flags around (x, p)
+    auto issue = [&](int p, S (&raw)[18], unsigned& smask) {
+        const RowIdx q = rows_of(p, ny);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
+                issue_pull<S>(src, plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc, bm + sc.xm,
+                              bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, raw);
+            }
+        }
+    };
+    // decode a pulled row and put its densities into ring slot `slot`
+    auto finish = [&](const S (&raw)[18], unsigned smask, C (&f)[2][9], int slot) {
+        C nA = C(0), nB = C(0);
+        if (sc.dcol && !SOL(smask, 0, 0)) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[k][i] = dec(raw[k * 9 + i], cx.sh.v[k][grp(i)]);
+            nA = dens9(f[0]);
+            nB = dens9(f[1]);
+        }
+        sd[slot][0][t] = nA;
+        sd[slot][1][t] = nB;
+    };
+
+    const int y0 = tl.y0, y1 = tl.y1;
+    C fc[2][9], fn[2][9];
+    S rn[18], rn2[18];
+    unsigned smc = 0, smn = 0, smn2 = 0;
+    issue(y0 - 1, rn, smn);
+    finish(rn, smn, fn, 0);            // halo row: densities only
+    issue(y0, rn, smc);
+    finish(rn, smc, fc, 1);
+    issue(y0 + 1, rn, smn);            // in flight into the loop
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        if (r + 2 <= y1) issue(r + 2, rn2, smn2);
+        finish(rn, smn, fn, s_p);      // row r + 1, loaded one iteration ago
+        __syncthreads();
+        if (sc.coll && !SOL(smc, 0, 0)) {
+            const RowIdx q = rows_of(r, ny);
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (unsigned)(q.rw * pitch + sc.xc),
+                                  MomOut{nullptr, nullptr, 0}, 0, ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
+        }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) rn[i] = rn2[i];
         smc = smn;
+        smn = smn2;
     }
 }
 
@@ -439,8 +880,8 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
             const RowIdx q = rows_of(p, ny);
             const unsigned m = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
             if (!SOL(m, 0, 0)) {
-                const long long bw = (long long)q.rw * pitch, bm = (long long)q.rm * pitch,
-                                bp = (long long)q.rp * pitch;
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
                 const long long own = bw + sc.xc;
                 S* st = stage + (size_t)(((p - y0 + 1) % D) * 18) * W + t;
 #pragma unroll
@@ -501,7 +942,7 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
         __syncthreads();
         if (sc.coll && !SOL(smc, 0, 0)) {
             const RowIdx q = rows_of(r, ny);
-            collide_node<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (long long)q.rw * pitch + sc.xc,
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (unsigned)(q.rw * pitch + sc.xc),
                                   MomOut{nullptr, nullptr, 0}, 0, ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
         }
 #pragma unroll
@@ -633,19 +1074,21 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
 
     // source row sequence number sq (row y0 - 2 + sq) lives in slot sq % S;
     // its k-th fill completes phase k & 1 of that slot's mbarrier
-    int issued = 0;   // meaningful in thread 0 only
-    auto issue_upto = [&](int last) {   // thread 0: issue every sq <= last not yet issued
+    int issued = 0;   // meaningful in warp 0 only (all its lanes agree)
+    // warp 0: issue every sq <= last not yet issued; lane q < 18 copies plane q
+    // (the order of the arrive.expect_tx and the completions does not matter)
+    auto issue_upto = [&](int last) {
         for (; issued <= last && issued < nsrc; ++issued) {
             const int sq = issued;
             const int slot = sq % kTmaSlots;
             int row = (y0 - 2 + sq) % ny;
             if (row < 0) row += ny;
             S* dslot = ring + (size_t)slot * TG::slot_elems;
-            mbar_expect_tx(&bars[slot], 18u * win_bytes);
-            const S* g = src + (long long)row * pitch + (x0 - OFF);
-#pragma unroll 1
-            for (int q = 0; q < 18; ++q)
-                bulk_g2s(dslot + q * WIN, g + (long long)q * plane, win_bytes, &bars[slot]);
+            if (t == 0) mbar_expect_tx(&bars[slot], 18u * win_bytes);
+            if (t < 18) {
+                const S* g = src + (long long)row * pitch + (x0 - OFF);
+                bulk_g2s(dslot + t * WIN, g + (long long)t * plane, win_bytes, &bars[slot]);
+            }
         }
     };
     bool timed_out = false;
@@ -691,7 +1134,7 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
     unsigned smc = 0, smn = 0;
     bool abort_cta = false;
     // prologue: fill the whole ring, then pull rows y0 - 1 and y0 (sq 0..3)
-    if (t == 0) issue_upto(kTmaSlots - 1);
+    if (t < 32) issue_upto(kTmaSlots - 1);
     for (int sq = 0; sq < 4; ++sq) wait_row(sq);
     if (!timed_out) {
         pull_row(y0 - 1, fn, smn, 0);
@@ -703,7 +1146,7 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
         const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
         // every thread finished the pulls that read source rows <= r - y0 + 1
         // (previous barrier): refill their slots up to two rows past the next need
-        if (t == 0) {
+        if (t < 32) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             issue_upto(r - y0 + 6);
         }
@@ -715,7 +1158,7 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
         }
         if (coll && !SOL(smc, 0, 0)) {
             const RowIdx q = rows_of(r, ny);
-            collide_node<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, sdc, dst, plane, (long long)q.rw * pitch + xc,
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, sdc, dst, plane, (unsigned)(q.rw * pitch + xc),
                                   MomOut{nullptr, nullptr, 0}, 0, ghost_r(xc, nx), ghost_l(xc, nx));
         }
 #pragma unroll

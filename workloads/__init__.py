@@ -99,12 +99,15 @@ def params(G: float, tau_A: float, tau_B: float, G_Aw: float = 0.0, G_Bw: float 
 
 def capillary_run(L_cap: int, H: int, G: float, tau_A: float, tau_B: float, G_Aw: float,
                   G_Bw: float = 0.0) -> dict:
-    """Capillary in the right half of a 2 L_cap x (H + 2) box; liquid fills the
-    reservoir and the first quarter of the capillary."""
+    """Capillary in the right half of a 2 L_cap x (H + 2) box (Fig. 1).  The
+    reservoir (left half, periodic top and bottom) holds gas on [0, L_cap/2)
+    and liquid from L_cap/2 to the front at L_cap + L_cap/4, so the gas that
+    the liquid displaces leaves the capillary through the periodic east side
+    into the reservoir's gas, across a flat reservoir interface."""
     nx, ny = 2 * L_cap, H + 2
     geom = capillary_geometry(nx, ny, L_cap, 2 * L_cap, 0, H + 1)
     x_front = L_cap + L_cap // 4
-    return dict(geom=geom, params=params(G, tau_A, tau_B, G_Aw, G_Bw), init=("slab", 0, x_front))
+    return dict(geom=geom, params=params(G, tau_A, tau_B, G_Aw, G_Bw), init=("slab", L_cap // 2, x_front))
 
 
 # ---- the five workload families ------------------------------------------
