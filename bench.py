@@ -205,7 +205,7 @@ def measure_batched(world: int, rank: int, stream, precision: str = "f32", steps
     total_nodes = nodes * world if world > 1 else nodes
     return {"value": total_nodes / (ms * 1e-3) / 1e9, "unit": "GLUPS", "runs": len(allruns),
             "nodes": total_nodes, "ms_per_step": ms, "precision": precision,
-            "schedule": {"tile": list(sched[:2]), "kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch"][sched[2]]},
+            "schedule": {"tile": list(sched[:2]), "kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair", "node-tile"][sched[2]]},
             "runs_per_hour_at_2e4_steps": len(allruns) * 3600.0 / (ms * 1e-3 * 2e4),
             "alg_GBs": nodes * world * BYTES_PER_NODE[precision] / (ms * 1e-3) / 1e9 if world > 1 else
             nodes * BYTES_PER_NODE[precision] / (ms * 1e-3) / 1e9,
@@ -334,7 +334,7 @@ def main():
     with torch.cuda.stream(stream):
         lat = Lattice(run, precision=args.precision, log_every=log_every, log_capacity=4096, autotune=True,
                       stream=stream)
-        lat.step(400)          # autotuning: real steps, every schedule gives the same bits
+        lat.step(600)          # autotuning: real steps, every schedule gives the same bits
         lat.step(args.warmup)
         lat.sync()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
@@ -408,7 +408,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [g["nx"], g["ny"]], "fluid_nodes": fluid_nodes,
                    "precision": args.precision, "tile": list(sched[:2]),
-                   "step_kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch"][sched[2]], "log_every": log_every,
+                   "step_kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair", "node-tile"][sched[2]], "log_every": log_every,
                    "l2": "flushed (256 MB write) between timed steps", "state_finite": finite,
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,

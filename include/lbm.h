@@ -256,6 +256,10 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 #define LBM_KERNEL_PIPELINED 3   /* register pull, the next row's loads issued before the collision */
 #define LBM_KERNEL_SPLIT 4       /* one thread per species and node (2 tile_w threads per CTA) */
 #define LBM_KERNEL_PREFETCH 5    /* register pull, rows streamed into L2 ahead by bulk prefetches */
+#define LBM_KERNEL_SMEM 6        /* register pull, pulled rows parked in shared memory: 64 registers */
+#define LBM_KERNEL_PAIR 7        /* two columns per thread, vector loads and stores; nx >= 4 */
+#define LBM_KERNEL_TILE 8        /* one node per thread, W x (R + 2) tiles: W in {32, 64}, R in {6, 14, 30}
+                                    (W = 64: R in {6, 14}); nx >= 4 */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 

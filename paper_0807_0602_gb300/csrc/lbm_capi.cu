@@ -46,7 +46,10 @@ struct lbm_s {
     int kvar = 0, depth = 4;       // step kernel: 0 register pull, 1 cp.async stages of depth D, 2 TMA ring,
                                    // 3 register pull with the next row's loads in flight,
                                    // 4 species split over two threads per node,
-                                   // 5 register pull with bulk L2 prefetch of rows ahead
+                                   // 5 register pull with bulk L2 prefetch of rows ahead,
+                                   // 6 register pull with the pulled rows parked in shared memory,
+                                   // 7 two columns per thread with vector loads and stores,
+                                   // 8 one node per thread over a W x (R + 2) tile
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -158,7 +161,9 @@ void build_tiles(lbm_t* h, int W, int R) {
     h->tile_begin.assign(h->nruns, 0);
     h->tile_count.assign(h->nruns, 0);
     // the TMA kernel collides W - 8 columns from x0 multiple of 8, the others W - 2
-    const int Wc = h->kvar == 2 ? W - 8 : W - 2;
+    // and the pair kernel 2W - 4 from an even x0
+    const int Wc = h->kvar == 2 ? W - 8 : (h->kvar == 7 ? 2 * W - 4 : W - 2);
+    // (the tile kernel: W - 2 columns and R rows, R fixed by its thread rows)
     for (int r = 0; r < h->nruns; ++r) {
         const RunDesc& rd = h->runs[r];
         const int Rr = std::max(1, std::min(R, rd.ny));
@@ -209,21 +214,52 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
                         [&](auto L) { return L.step_async(W, h->depth, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 2)
         return dispatch(h->precision,
-                        [&](auto L) { return L.step_tma(W, h->d_runs, h->d_tiles, nt, parity, h->d_err, s); });
+                        [&](auto L) { return L.step_tma(W, h->depth, h->d_runs, h->d_tiles, nt, parity, h->d_err, s); });
     if (h->kvar == 3)
         return dispatch(h->precision, [&](auto L) { return L.step_pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 4)
         return dispatch(h->precision, [&](auto L) { return L.step_split(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 5)
         return dispatch(h->precision, [&](auto L) { return L.step_l2pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 6)
+        return dispatch(h->precision, [&](auto L) { return L.step_smem(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 7)
+        return dispatch(h->precision, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 8)
+        return dispatch(h->precision,
+                        [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
     return dispatch(h->precision, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
+    if (R < 1 || kvar < 0 || kvar > 8) return false;
+    if (kvar == 8) {
+        // one node per thread: W x (R + 2) threads, pulls read the ghost columns
+        if (!((W == 32 && (R == 6 || R == 14 || R == 30)) || (W == 64 && (R == 6 || R == 14)))) return false;
+        for (const RunDesc& rd : h->runs)
+            if (rd.nx < 4) return false;
+        return true;
+    }
     if (W != 64 && W != 128 && W != 256) return false;
-    if (R < 1 || kvar < 0 || kvar > 5) return false;
     if (kvar == 1 && (h->precision == LBM_F16S || (depth != 3 && depth != 4))) return false;
+    // the shared-memory-staged kernel keeps 18 W populations per row parity in
+    // static shared memory: FP64 at W = 256 would exceed the 48 KB static limit
+    if (kvar == 6 && h->precision == LBM_F64 && W == 256) return false;
+    if (kvar == 7) {
+        // two columns per thread: 2W columns of staged populations per CTA
+        // (W <= 128, FP64 W = 64); pulls read the ghost columns: nx >= 4
+        if (W > 128 || (h->precision == LBM_F64 && W > 64)) return false;
+        for (const RunDesc& rd : h->runs)
+            if (rd.nx < 4) return false;
+    }
     if (kvar == 2) {
+        // ring of `depth` row slots of 18 windows of W - 8 + 32 / elem columns in
+        // dynamic shared memory (at most 227 KB), plus the density ring
+        if (depth != 4 && depth != 6 && depth != 8) return false;
+        if (W == 256 && depth == 8) return false;
+        const size_t e = h->elem, ce = h->precision == LBM_F64 ? 8 : 4;
+        const size_t win = (size_t)(W - 8) + 2 * (16 / e);
+        if ((size_t)depth * 18 * win * e + 8 * W * ce + 8 * (size_t)depth + 16 > sc::kMaxSmemPerCta) return false;
         // the TMA windows rely on two ghost columns each side: nx >= 4
         for (const RunDesc& rd : h->runs)
             if (rd.nx < 4) return false;
@@ -322,9 +358,15 @@ int autotune(lbm_t* h, int64_t* n) {
             cands.push_back({W, R, 3, 4});
             cands.push_back({W, R, 4, 4});
             cands.push_back({W, R, 5, 4});
-            if (schedule_ok(h, W, R, 2, 4)) cands.push_back({W, R, 2, 4});
+            if (schedule_ok(h, W, R, 6, 4)) cands.push_back({W, R, 6, 4});
+            if (schedule_ok(h, W, R, 7, 4)) cands.push_back({W, R, 7, 4});
+            for (int D : {4, 6, 8})
+                if (schedule_ok(h, W, R, 2, D)) cands.push_back({W, R, 2, D});
             if (W < 256 && schedule_ok(h, W, R, 1, 4)) cands.push_back({W, R, 1, 4});
         }
+    for (int W : {32, 64})
+        for (int R : {6, 14, 30})
+            if (schedule_ok(h, W, R, 8, 4)) cands.push_back({W, R, 8, 4});
     const int per = 6;
     if (*n < (int64_t)cands.size() * (per + 1)) return LBM_OK;  // too short to tune now
     cudaEvent_t e0, e1;
@@ -427,6 +469,9 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
     }
     char* arena = static_cast<char*>(dalloc(h, total));
     if (!arena) return fail(LBM_ENOMEM);
+    // padding columns are read (never used) by the pair kernel's unneeded
+    // halo nodes: keep them defined
+    if (cudaMemsetAsync(arena, 0, total, h->stream) != cudaSuccess) return fail(LBM_ECUDA);
 
     // per-run masks and initial fields
     h->runs.resize(n);

@@ -32,6 +32,9 @@ struct RunDesc {
 
 // A CTA's work: run, first collided column x0 (the CTA collides
 // min(W - 2, nx - x0) columns), rows [y0, y1).
+// opt-in shared memory per CTA on sm_103a (227 KB)
+constexpr size_t kMaxSmemPerCta = 232448;
+
 struct Tile {
     int run, x0, y0, y1;
 };
@@ -59,13 +62,19 @@ struct Launch {
                             cudaStream_t s);
     static cudaError_t step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s);
-    static cudaError_t step_tma(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+    static cudaError_t step_tma(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                 uint32_t* err, cudaStream_t s);
     static cudaError_t step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                cudaStream_t s);
     static cudaError_t step_split(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s);
     static cudaError_t step_l2pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s);
+    static cudaError_t step_smem(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s);
+    static cudaError_t step_pair(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s);
+    static cudaError_t step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);

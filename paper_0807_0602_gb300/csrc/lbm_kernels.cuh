@@ -109,6 +109,15 @@ template <> struct Shift<__half> {
     }
 };
 __device__ __forceinline__ constexpr int grp(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+// D2Q9 lattice vectors c_i (c_1 = (1, 0), c_2 = (0, 1), c_5 = (1, 1), c_6 = (-1, 1), ...)
+// and opposite directions
+__device__ __forceinline__ constexpr int cxo(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int cyo(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5); }
 
 struct Geo {
     int nx, cx0, cx1, yb, yt;
@@ -225,35 +234,32 @@ struct StepCtx {
     }
 };
 
-// Steps 2-7 at one fluid node of row `rw`, column `xc` (thread t of the
-// strip): densities of this and the neighbouring nodes come from the shared
-// ring (slots of rows r-1, r, r+1), the node's pulled populations from fc.
-// MODE 0 writes the post-collision populations, MODE 1 the whole-fluid
-// velocity rho u = sum_k j_k + (1/2) sum_k n_k a_k.
 // Offsets from column x to its ghost images: columns 0 and 1 are mirrored at
 // nx and nx + 1, columns nx - 2 and nx - 1 at -2 and -1 (0 = no image).
 __device__ __forceinline__ int ghost_r(int x, int nx) { return x < 2 ? nx : 0; }
 __device__ __forceinline__ int ghost_l(int x, int nx) { return x >= nx - 2 ? -nx : 0; }
 
-// Populations of columns 0, 1 and nx - 2, nx - 1 are also written to their
-// periodic images at x = nx, nx + 1 and x = -2, -1 (ghost columns), so that
-// every source row a later step reads is one contiguous window; gr / gl give
-// the offsets of those images from the node (0 = none).
-template <typename S, int W, int MODE, bool GH = true>
-__device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
-                                             const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
-                                             S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
-                                             long long mo_idx, int gr = 0, int gl = 0) {
+// Steps 2-3 at one fluid node: densities (shared ring), momenta and the
+// accelerations a_k of both species.
+template <typename S>
+struct NodeState {
+    using C = typename Prec<S>::C;
+    C n[2], jx[2], jy[2], ax[2], ay[2];
+};
+
+template <typename S, int W>
+__device__ __forceinline__ void node_state(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+                                           const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
+                                           NodeState<S>& ns) {
     using C = typename Prec<S>::C;
     using Wc = Wt<C>;
     using A = Ar<C>;
-    C n[2], jx[2], jy[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const C(&f)[9] = fc[k];
-        n[k] = sd[s_0][k][t];
-        jx[k] = A::add(A::sub(A::sub(A::add(A::sub(f[1], f[3]), f[5]), f[6]), f[7]), f[8]);
-        jy[k] = A::sub(A::sub(A::add(A::add(A::sub(f[2], f[4]), f[5]), f[6]), f[7]), f[8]);
+        ns.n[k] = sd[s_0][k][t];
+        ns.jx[k] = A::add(A::sub(A::sub(A::add(A::sub(f[1], f[3]), f[5]), f[6]), f[7]), f[8]);
+        ns.jy[k] = A::sub(A::sub(A::add(A::add(A::sub(f[2], f[4]), f[5]), f[6]), f[7]), f[8]);
     }
     // wall sum of Eq. 11, the same for both species
     C Wx = C(0), Wy = C(0);
@@ -269,7 +275,6 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
     }
     // bulk force of Eq. 9 from the neighbour densities of the other species:
     // S = ((((w1 n1 - w1 n3) + w5 n5) - w5 n6) - w5 n7) + w5 n8 (and y)
-    C ax[2], ay[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int kb = 1 - k;
@@ -285,21 +290,22 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
         Sy = A::fma(Wc::w5, n6, Sy);
         Sy = A::fma(-Wc::w5, n7, Sy);
         Sy = A::fma(-Wc::w5, n8, Sy);
-        ax[k] = A::add(A::sub(-A::mul(cx.G, Sx), A::mul(cx.Gw[k], Wx)), cx.gx);
-        ay[k] = A::add(A::sub(-A::mul(cx.G, Sy), A::mul(cx.Gw[k], Wy)), cx.gy);
+        ns.ax[k] = A::add(A::sub(-A::mul(cx.G, Sx), A::mul(cx.Gw[k], Wx)), cx.gx);
+        ns.ay[k] = A::add(A::sub(-A::mul(cx.G, Sy), A::mul(cx.Gw[k], Wy)), cx.gy);
     }
-    if (MODE == 1) {
-        const C ntot = A::add(n[0], n[1]);
-        const C fxs = A::fma(n[0], ax[0], A::mul(n[1], ax[1]));
-        const C fys = A::fma(n[0], ay[0], A::mul(n[1], ay[1]));
-        mo.ux[mo_idx] = (double)A::div(A::fma(C(0.5), fxs, A::add(jx[0], jx[1])), ntot);
-        mo.uy[mo_idx] = (double)A::div(A::fma(C(0.5), fys, A::add(jy[0], jy[1])), ntot);
-        return;
-    }
+}
+
+// Steps 4-7: common velocity, shifted equilibria and BGK relaxation.
+template <typename S>
+__device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9],
+                                      const NodeState<S>& ns, typename Prec<S>::C (&fnew)[2][9]) {
+    using C = typename Prec<S>::C;
+    using Wc = Wt<C>;
+    using A = Ar<C>;
     // common velocity (Eq. 8) and shifted equilibrium velocities (Eq. 7)
-    const C den = A::fma(n[0], cx.itau[0], A::mul(n[1], cx.itau[1]));
-    const C numx = A::fma(jx[0], cx.itau[0], A::mul(jx[1], cx.itau[1]));
-    const C numy = A::fma(jy[0], cx.itau[0], A::mul(jy[1], cx.itau[1]));
+    const C den = A::fma(ns.n[0], cx.itau[0], A::mul(ns.n[1], cx.itau[1]));
+    const C numx = A::fma(ns.jx[0], cx.itau[0], A::mul(ns.jx[1], cx.itau[1]));
+    const C numy = A::fma(ns.jy[0], cx.itau[0], A::mul(ns.jy[1], cx.itau[1]));
     C Ux, Uy;
     if constexpr (kCanonical<C>) {
         Ux = A::div(numx, den);
@@ -311,12 +317,12 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const C ux = A::fma(cx.tau[k], ax[k], Ux);
-        const C uy = A::fma(cx.tau[k], ay[k], Uy);
+        const C ux = A::fma(cx.tau[k], ns.ax[k], Ux);
+        const C uy = A::fma(cx.tau[k], ns.ay[k], Uy);
         const C usq = A::fma(ux, ux, A::mul(uy, uy));
         const C b = A::mul(C(1.5), usq);
-        const C wn0 = A::mul(Wc::w0, n[k]), wn1 = A::mul(Wc::w1, n[k]), wn5 = A::mul(Wc::w5, n[k]);
-        C fnew[9];
+        const C nk = ns.n[k];
+        const C wn0 = A::mul(Wc::w0, nk), wn1 = A::mul(Wc::w1, nk), wn5 = A::mul(Wc::w5, nk);
         if constexpr (kCanonical<C>) {
             const C cu[9] = {C(0), ux, uy, -ux, -uy, A::add(ux, uy), A::add(-ux, uy), A::sub(-ux, uy), A::sub(ux, uy)};
 #pragma unroll
@@ -326,7 +332,7 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
                 // Eqs. 3-5: wn (((1 + 3 c) + 4.5 (c c)) - b)
                 const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
                 const C f = fc[k][i];
-                fnew[i] = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
+                fnew[k][i] = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
             }
         } else {
             // Eqs. 3-5 by opposite pairs: feq(+-c) = wn (1 + 4.5 c^2 - b) +- 3 wn c;
@@ -342,23 +348,57 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
                 const C c = cp[q];
                 const C sy = A::mul(wn, A::fma(C(4.5), A::mul(c, c), base));
                 const C an = A::mul(A::mul(C(3), wn), c);
-                fnew[ia[q]] = A::fma(A::add(sy, an), it, A::mul(fc[k][ia[q]], om));
-                fnew[ib[q]] = A::fma(A::sub(sy, an), it, A::mul(fc[k][ib[q]], om));
-                moving = A::add(moving, A::add(fnew[ia[q]], fnew[ib[q]]));
+                fnew[k][ia[q]] = A::fma(A::add(sy, an), it, A::mul(fc[k][ia[q]], om));
+                fnew[k][ib[q]] = A::fma(A::sub(sy, an), it, A::mul(fc[k][ib[q]], om));
+                moving = A::add(moving, A::add(fnew[k][ia[q]], fnew[k][ib[q]]));
             }
             // the collision conserves n_k: the rest population takes what the
             // moving ones leave, so FP32 rounding does not bias the mass
-            fnew[0] = A::sub(n[k], moving);
+            fnew[k][0] = A::sub(nk, moving);
+            (void)wn0;
         }
+    }
+}
+
+// Steps 2-7 at one fluid node of row `rw`, column `xc` (thread t of the
+// strip): densities of this and the neighbouring nodes come from the shared
+// ring (slots of rows r-1, r, r+1), the node's pulled populations from fc.
+// MODE 0 writes the post-collision populations, MODE 1 the whole-fluid
+// velocity rho u = sum_k j_k + (1/2) sum_k n_k a_k.
+// Populations of columns 0, 1 and nx - 2, nx - 1 are also written to their
+// periodic images at x = nx, nx + 1 and x = -2, -1 (ghost columns), so that
+// every source row a later step reads is one contiguous window; gr / gl give
+// the offsets of those images from the node (0 = none).
+template <typename S, int W, int MODE, bool GH = true>
+__device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+                                             const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
+                                             S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
+                                             long long mo_idx, int gr = 0, int gl = 0) {
+    using C = typename Prec<S>::C;
+    using A = Ar<C>;
+    NodeState<S> ns;
+    node_state<S, W>(cx, fc, m, sd, s_m, s_0, s_p, t, ns);
+    if (MODE == 1) {
+        const C ntot = A::add(ns.n[0], ns.n[1]);
+        const C fxs = A::fma(ns.n[0], ns.ax[0], A::mul(ns.n[1], ns.ax[1]));
+        const C fys = A::fma(ns.n[0], ns.ay[0], A::mul(ns.n[1], ns.ay[1]));
+        mo.ux[mo_idx] = (double)A::div(A::fma(C(0.5), fxs, A::add(ns.jx[0], ns.jx[1])), ntot);
+        mo.uy[mo_idx] = (double)A::div(A::fma(C(0.5), fys, A::add(ns.jy[0], ns.jy[1])), ntot);
+        return;
+    }
+    C fnew[2][9];
+    relax<S>(cx, fc, ns, fnew);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
         S* d = dst + ((unsigned)(k * 9) * plane + o);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) enc(d + (unsigned)i * plane, fnew[i], cx.sh.v[k][grp(i)]);
+        for (int i = 0; i < 9; ++i) enc(d + (unsigned)i * plane, fnew[k][i], cx.sh.v[k][grp(i)]);
         if (GH) {   // ghost images of the edge columns (rare)
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 S* p = d + (unsigned)i * plane;
-                if (gr) enc(p + gr, fnew[i], cx.sh.v[k][grp(i)]);
-                if (gl) enc(p + gl, fnew[i], cx.sh.v[k][grp(i)]);
+                if (gr) enc(p + gr, fnew[k][i], cx.sh.v[k][grp(i)]);
+                if (gl) enc(p + gl, fnew[k][i], cx.sh.v[k][grp(i)]);
             }
         }
     }
@@ -712,6 +752,359 @@ __global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(c
     }
 }
 
+// ---- shared-memory-staged register variant -------------------------------------
+// k_step's march with the pulled populations of a row parked in shared
+// memory (each thread's own slot, double-buffered by row parity) until that
+// row is collided, instead of held in registers across the next row's pull.
+// Only the row being loaded lives in registers, so the kernel fits in 64
+// registers and 1024 threads per SM: twice the nodes in flight of k_step.
+template <typename S, int W>
+constexpr int kSmemMinBlocks = (sizeof(typename Prec<S>::C) == 8 || W >= 1024) ? 1 : 1024 / W;
+
+template <typename S, int W>
+__global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const RunDesc* __restrict__ runs,
+                                                                        const Tile* __restrict__ tiles,
+                                                                        int parity) {
+    using C = typename Prec<S>::C;
+    __shared__ C sd[4][2][W];
+    __shared__ C ps[2][18][W];   // [row parity][population][thread]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const long long plane = rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const StripCols sc(tl.x0, nx, W, t);
+
+    // pull row r into ps[r & 1] (own slot) and its densities into sd[slot]
+    auto pull_row = [&](int r, unsigned& smask, int slot) {
+        const RowIdx q = rows_of(r, ny);
+        C nA = C(0), nB = C(0);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
+                C f[2][9];
+                pull_node<S>(src, (unsigned)plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc,
+                             bm + sc.xm, bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, cx.sh, f);
+                nA = dens9(f[0]);
+                nB = dens9(f[1]);
+                if (sc.coll) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) ps[r & 1][k * 9 + i][t] = f[k][i];
+                }
+            }
+        }
+        sd[slot][0][t] = nA;
+        sd[slot][1][t] = nB;
+    };
+
+    const int y0 = tl.y0, y1 = tl.y1;
+    unsigned smc = 0, smn = 0;
+    pull_row(y0 - 1, smn, 0);
+    pull_row(y0, smc, 1);
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        pull_row(r + 1, smn, s_p);
+        __syncthreads();
+        if (sc.coll && !SOL(smc, 0, 0)) {
+            const RowIdx q = rows_of(r, ny);
+            C fc[2][9];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fc[k][i] = ps[r & 1][k * 9 + i][t];
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, (unsigned)plane,
+                                 (unsigned)(q.rw * pitch + sc.xc), MomOut{nullptr, nullptr, 0}, 0,
+                                 ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
+        }
+        smc = smn;
+    }
+}
+
+// ---- two-columns-per-thread variant ---------------------------------------------
+// Thread t of a CTA of W threads owns the column pair (xa, xa + 1),
+// xa = x0 - 2 + 2t with x0 even, and marches down the rows of its tile like
+// k_step_smem.  Per population plane a pair needs one address: unshifted
+// planes are read with one vector load (8 bytes in FP32), x-shifted ones with
+// two loads at immediate offsets, and the post-collision populations go out
+// as one vector store per plane.  The strip collides the 2W - 4 columns
+// [x0, x0 + 2W - 4); column x0 - 1 (thread 0) and x0 + ncols are its halo.
+// Pulls read the periodic images of columns -2, -1, nx, nx + 1 from the ghost
+// columns (nx >= 4), so the load path never wraps in x.  Nodes next to a
+// solid replace the pulled values by bounce-back loads of their own node.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    static __device__ __forceinline__ void ld(const float* p, float& a, float& b, float) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, float a, float b, float) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+};
+template <> struct Pair<double> {
+    static __device__ __forceinline__ void ld(const double* p, double& a, double& b, double) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st(double* p, double a, double b, double) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    }
+};
+template <> struct Pair<__half> {
+    static __device__ __forceinline__ void ld(const __half* p, float& a, float& b, float sh) {
+        const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+        a = dec(__ushort_as_half((unsigned short)(u & 0xffffu)), sh);
+        b = dec(__ushort_as_half((unsigned short)(u >> 16)), sh);
+    }
+    static __device__ __forceinline__ void st(__half* p, float a, float b, float sh) {
+        const unsigned lo = __half_as_ushort(__float2half_rn(__fsub_rn(a, sh)));
+        const unsigned hi = __half_as_ushort(__float2half_rn(__fsub_rn(b, sh)));
+        *reinterpret_cast<unsigned*>(p) = lo | (hi << 16);
+    }
+};
+
+
+// resident CTAs per SM the register allocation aims at: 512 threads (128
+// registers) for W = 64, 640 (96 registers) for W = 128; shared memory
+// (45 KB per 128 threads) allows at most 640
+template <typename S, int W>
+constexpr int kPairMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : (W >= 128 ? 5 : 8);
+
+template <typename S, int W>
+__global__ void __launch_bounds__(W, (kPairMinBlocks<S, W>)) k_step_pair(const RunDesc* __restrict__ runs,
+                                                                        const Tile* __restrict__ tiles, int parity) {
+    using C = typename Prec<S>::C;
+    constexpr int NC = 2 * W;                       // ring columns: strip column c <-> x = x0 - 2 + c
+    __shared__ __align__(16) C sd[4][2][NC];
+    __shared__ __align__(16) C ps[2][18][NC];       // [row parity][population][strip column]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const unsigned plane = (unsigned)rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x;
+    const int x0 = tl.x0;
+    const int ncols = min(NC - 4, nx - x0);
+    const int c0 = 2 * t;                           // strip column of node 0
+    const int xa = x0 - 2 + c0;                     // unwrapped column of node 0, in [-2, nx + 1] when active
+    const bool act = c0 <= ncols + 2;
+    bool need[2], coll[2];
+    int xw[2], xmw[2], xpw[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int c = c0 + j;
+        need[j] = act && c >= 1 && c <= ncols + 2;
+        coll[j] = act && c >= 2 && c < ncols + 2;
+        int x = xa + j;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        if (!act) x = 0;
+        xw[j] = x;
+        xmw[j] = x == 0 ? nx - 1 : x - 1;
+        xpw[j] = x == nx - 1 ? 0 : x + 1;
+    }
+
+    // pull row r for both nodes, densities into ring slot `slot`, populations
+    // into ps[r & 1] when `stage`
+    auto pull_row = [&](int r, unsigned (&sm)[2], int slot, bool stage) {
+        C n[2][2] = {{C(0), C(0)}, {C(0), C(0)}};   // [node][species]
+        sm[0] = sm[1] = 0;
+        if (act) {
+            const RowIdx q = rows_of(r, ny);
+            sm[0] = nbr_solid(geo, xmw[0], xw[0], xpw[0], q.rm, q.rw, q.rp);
+            sm[1] = nbr_solid(geo, xmw[1], xw[1], xpw[1], q.rm, q.rw, q.rp);
+            const S* Pw = src + (q.rw * pitch + xa);
+            const S* Pm = src + (q.rm * pitch + xa);
+            const S* Pp = src + (q.rp * pitch + xa);
+            C f[2][2][9];   // [node][species][direction]
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const S* P = (cyo(i) == 0 ? Pw : (cyo(i) > 0 ? Pm : Pp)) + (unsigned)(9 * k + i) * plane;
+                    const C sh = cx.sh.v[k][grp(i)];
+                    if (cxo(i) == 0) {
+                        Pair<S>::ld(P, f[0][k][i], f[1][k][i], sh);
+                    } else if (cxo(i) > 0) {   // source column x - 1
+                        f[0][k][i] = dec(ldg(P - 1), sh);
+                        f[1][k][i] = dec(ldg(P), sh);
+                    } else {                   // source column x + 1
+                        f[0][k][i] = dec(ldg(P + 1), sh);
+                        f[1][k][i] = dec(ldg(P + 2), sh);
+                    }
+                }
+            if (sm[0] | sm[1]) {   // half-way bounce-back next to a solid (step 1)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    if (sm[j] && !SOL(sm[j], 0, 0)) {
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+#pragma unroll
+                            for (int i = 1; i < 9; ++i)
+                                if (SOL(sm[j], -cyo(i), -cxo(i)))
+                                    f[j][k][i] = dec(ldg(Pw + (unsigned)(9 * k + opp(i)) * plane + j),
+                                                     cx.sh.v[k][grp(i)]);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (need[j] && !SOL(sm[j], 0, 0)) {
+                    n[j][0] = dens9(f[j][0]);
+                    n[j][1] = dens9(f[j][1]);
+                }
+            if (stage) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        ps[r & 1][9 * k + i][c0] = f[0][k][i];
+                        ps[r & 1][9 * k + i][c0 + 1] = f[1][k][i];
+                    }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            sd[slot][k][c0] = n[0][k];
+            sd[slot][k][c0 + 1] = n[1][k];
+        }
+    };
+
+    const int y0 = tl.y0, y1 = tl.y1;
+    unsigned smc[2] = {0, 0}, smn[2] = {0, 0};
+    pull_row(y0 - 1, smn, 0, false);
+    pull_row(y0, smc, 1, true);
+    for (int r = y0; r < y1; ++r) {
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
+        pull_row(r + 1, smn, s_p, r + 1 < y1);
+        __syncthreads();
+        const bool f0 = coll[0] && !SOL(smc[0], 0, 0), f1 = coll[1] && !SOL(smc[1], 0, 0);
+        if (f0 | f1) {
+            const int rw = rows_of(r, ny).rw;
+            S* Q = dst + (rw * pitch + xa);
+            C fn0[2][9], fn1[2][9];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (!(j == 0 ? f0 : f1)) continue;
+                C fc[2][9];
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fc[k][i] = ps[r & 1][9 * k + i][c0 + j];
+                NodeState<S> ns;
+                node_state<S, NC>(cx, fc, smc[j], sd, s_m, s_0, s_p, c0 + j, ns);
+                relax<S>(cx, fc, ns, j == 0 ? fn0 : fn1);
+            }
+            if (f0 & f1) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        Pair<S>::st(Q + (unsigned)(9 * k + i) * plane, fn0[k][i], fn1[k][i], cx.sh.v[k][grp(i)]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        S* d = Q + (unsigned)(9 * k + i) * plane;
+                        if (f0) enc(d, fn0[k][i], cx.sh.v[k][grp(i)]);
+                        if (f1) enc(d + 1, fn1[k][i], cx.sh.v[k][grp(i)]);
+                    }
+            }
+            // ghost images of the edge columns (rare)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int gr = ghost_r(xw[j], nx), gl = ghost_l(xw[j], nx);
+                if ((j == 0 ? f0 : f1) && (gr | gl)) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            S* d = Q + (unsigned)(9 * k + i) * plane + j;
+                            const C v = j == 0 ? fn0[k][i] : fn1[k][i];
+                            if (gr) enc(d + gr, v, cx.sh.v[k][grp(i)]);
+                            if (gl) enc(d + gl, v, cx.sh.v[k][grp(i)]);
+                        }
+                }
+            }
+        }
+        smc[0] = smn[0];
+        smc[1] = smn[1];
+    }
+}
+
+// ---- one-node-per-thread tile variant ----------------------------------------------
+// A CTA of W x TY threads pulls the W x TY nodes of columns x0 - 1 .. x0 + W - 2
+// and rows y0 - 1 .. y0 + TY - 2 at once (every thread's 18 loads in flight
+// together, no march), puts their densities in shared memory, and after one
+// __syncthreads collides the (W - 2) x (TY - 2) interior.  The halo nodes cost
+// redundant pulls (L2 hits) instead of serial row latency.  Pulls read the
+// ghost columns, so no x index wraps on the load path (nx >= 4).
+template <typename S, int W, int TY>
+constexpr int kTileMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 1024 / (W * TY);   // 64 registers
+
+template <typename S, int W, int TY>
+__global__ void __launch_bounds__(W * TY, (kTileMinBlocks<S, W, TY>)) k_step_tile(const RunDesc* __restrict__ runs,
+                                                                                const Tile* __restrict__ tiles,
+                                                                                int parity) {
+    using C = typename Prec<S>::C;
+    __shared__ C sd[TY][2][W];   // [tile row][species][tile column]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const unsigned plane = (unsigned)rd.plane;
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    const int tx = threadIdx.x % W, ty = threadIdx.x / W;
+    const int x = tl.x0 - 1 + tx;                          // unwrapped column, in [-1, nx] when active
+    const int r = tl.y0 - 1 + ty;                          // unwrapped row, in [-1, ny] when active
+    const bool act = x <= min(tl.x0 + W - 2, nx) && r <= tl.y1;
+    StepCtx<S> cx;
+    cx.load(rd);
+    const RowIdx q = rows_of(act ? r : 0, ny);
+    const int xw = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    unsigned m = 0;
+    C f[2][9];
+    C nA = C(0), nB = C(0);
+    if (act) {
+        const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+        m = nbr_solid(geo, xw == 0 ? nx - 1 : xw - 1, xw, xw == nx - 1 ? 0 : xw + 1, q.rm, q.rw, q.rp);
+        if (!SOL(m, 0, 0)) {
+            // offsets from column -2, so that every offset is non-negative
+            const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch), bp = (unsigned)(q.rp * pitch);
+            const unsigned xo = (unsigned)(x + 2);
+            pull_node<S>(src - 2, plane, bw + xo, bw + (xo - 1), bw + (xo + 1), bm + xo, bp + xo, bm + (xo - 1),
+                         bm + (xo + 1), bp + (xo - 1), bp + (xo + 1), m, cx.sh, f);
+            nA = dens9(f[0]);
+            nB = dens9(f[1]);
+        }
+    }
+    sd[ty][0][tx] = nA;
+    sd[ty][1][tx] = nB;
+    __syncthreads();
+    const bool coll = act && tx >= 1 && tx < W - 1 && x < nx && ty >= 1 && ty < TY - 1 && r < tl.y1;
+    if (coll && !SOL(m, 0, 0))
+        collide_any<S, W, 0>(cx, f, m, sd, ty - 1, ty, ty + 1, tx, static_cast<S*>(rd.buf[parity ^ 1]), plane,
+                             (unsigned)(q.rw * pitch + xw), MomOut{nullptr, nullptr, 0}, 0, ghost_r(xw, nx),
+                             ghost_l(xw, nx));
+}
+
 // ---- software-pipelined register variant ------------------------------------
 // k_step with the loads of row r + 2 issued (into raw registers) before row
 // r + 1 is decoded and row r collided: each row's HBM latency overlaps a
@@ -955,12 +1348,17 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
 }
 
 // ---- TMA-staged variant ------------------------------------------------------
-// One elected thread streams every source row the CTA needs into an S-slot
-// ring of shared memory with bulk copies (cp.async.bulk, one per population
-// plane and row: a contiguous window of the row thanks to the ghost columns),
-// completing on one mbarrier per slot; the copies run P rows ahead of the row
-// being pulled, so HBM reads are in flight without holding registers.
-// Threads then pull from shared memory at fixed offsets.
+// Bulk copies (cp.async.bulk, issued by 18 lanes of warp 0, one population
+// plane each) stream the source data of every row the CTA pulls into a ring
+// of D slots of shared memory, one slot per pulled row: slot p holds plane i
+// of source row p - c_iy (a contiguous window of that row, thanks to the
+// ghost columns), completing on the slot's mbarrier.  Row p's slot is read
+// twice: by the pull that feeds the density ring (iteration p - 1) and by the
+// collision of row p (iteration p), which re-reads its populations from the
+// slot instead of holding them in registers.  A slot is refilled with row
+// p + D once the barrier of iteration p + 1 has passed, so D - 2 rows are in
+// flight beyond the one being pulled and the HBM reads need no registers.
+// All shared-memory reads of a row use compile-time offsets from one base.
 //
 // Column mapping: a CTA collides the Wc = W - 8 columns [x0, x0 + Wc)
 // (x0 a multiple of 8, so global stores of a warp start on a 32-byte
@@ -971,8 +1369,6 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
 // Every mbarrier wait is bounded: a thread that gives up sets a flag, the
 // per-row __syncthreads_or makes the exit block-uniform, the CTA drains the
 // copies it issued (bounded again) and records ERR_TIMEOUT.
-constexpr int kTmaSlots = 5;           // S: ring slots (source rows)
-constexpr int kTmaAhead = 5;           // P: rows issued ahead of the first needed one
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s of SM clock per wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1010,34 +1406,66 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
-template <typename S, int W>
+template <typename S, int W, int D>
 struct TmaGeom {
     static constexpr int Wc = W - 8;                      // collided columns per CTA
     static constexpr int OFF = 16 / (int)sizeof(S);       // window starts OFF columns before x0
     static constexpr int WIN = Wc + 2 * OFF;              // window width (elements), 16-byte multiple
     static constexpr size_t slot_elems = (size_t)18 * WIN;
+    static constexpr size_t ring_bytes = (size_t)D * slot_elems * sizeof(S);
     static constexpr size_t smem_bytes() {
-        return (size_t)kTmaSlots * slot_elems * sizeof(S) + 4 * 2 * W * sizeof(typename Prec<S>::C) +
-               kTmaSlots * sizeof(uint64_t) + 16;
+        return ring_bytes + 4 * 2 * W * sizeof(typename Prec<S>::C) + D * sizeof(uint64_t) + 16;
     }
 };
 
-template <typename S, int W>
+// Pulled populations of one node from a ring slot: P points at the node's
+// column in plane 0 of the slot (row offsets c_iy were applied by the copy).
+template <typename S, int WIN>
+__device__ __forceinline__ void pull_slot(const S* P, unsigned m, const Shift<S>& sh, typename Prec<S>::C (&f)[2][9]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const S* q = P + k * 9 * WIN;
+        f[k][0] = dec(q[0], sh.v[k][0]);
+        f[k][1] = dec(q[1 * WIN - 1], sh.v[k][1]);
+        f[k][2] = dec(q[2 * WIN], sh.v[k][1]);
+        f[k][3] = dec(q[3 * WIN + 1], sh.v[k][1]);
+        f[k][4] = dec(q[4 * WIN], sh.v[k][1]);
+        f[k][5] = dec(q[5 * WIN - 1], sh.v[k][2]);
+        f[k][6] = dec(q[6 * WIN + 1], sh.v[k][2]);
+        f[k][7] = dec(q[7 * WIN + 1], sh.v[k][2]);
+        f[k][8] = dec(q[8 * WIN - 1], sh.v[k][2]);
+    }
+}
+
+// pull_slot next to a solid: bounce-back takes the node's own opposite
+// population F_opp(i)(x), read from the source buffer (gown: the node in
+// plane 0), since the slot holds the planes of other rows for c_iy != 0.
+template <typename S, int WIN>
+__device__ __forceinline__ void pull_slot_bb(const S* P, unsigned m, const Shift<S>& sh, const S* __restrict__ gown,
+                                             unsigned plane, typename Prec<S>::C (&f)[2][9]) {
+    pull_slot<S, WIN>(P, m, sh, f);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            if (SOL(m, -cyo(i), -cxo(i))) f[k][i] = dec(ldg(gown + (unsigned)(9 * k + opp(i)) * plane), sh.v[k][grp(i)]);
+}
+
+template <typename S, int W, int D>
 __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
                                                 int parity, uint32_t* __restrict__ err) {
     using C = typename Prec<S>::C;
-    using TG = TmaGeom<S, W>;
+    using TG = TmaGeom<S, W, D>;
     constexpr int Wc = TG::Wc, OFF = TG::OFF, WIN = TG::WIN;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    S* ring = reinterpret_cast<S*>(smem_raw);                                         // [S][18][WIN]
-    C(*sd)[2][W] = reinterpret_cast<C(*)[2][W]>(smem_raw + kTmaSlots * TG::slot_elems * sizeof(S));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kTmaSlots * TG::slot_elems * sizeof(S) +
-                                                 4 * 2 * W * sizeof(C));
+    S* ring = reinterpret_cast<S*>(smem_raw);                                              // [D][18][WIN]
+    C(*sd)[2][W] = reinterpret_cast<C(*)[2][W]>(smem_raw + TG::ring_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + TG::ring_bytes + 4 * 2 * W * sizeof(C));
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
-    const long long plane = rd.plane;
+    const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
@@ -1060,68 +1488,54 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
     const int xm = xc == 0 ? nx - 1 : xc - 1;
     const int xp = xc == nx - 1 ? 0 : xc + 1;
     const int sdc = j + 1;                 // density ring column
-    const int wc = j + OFF;                // column of this node inside a window
+    const int wc = (dcol ? j : 0) + OFF;   // column of this node inside a window
     // window bytes of one plane row, clipped to the allocated row
     const int win_elems = min(WIN, (pitch - LBM_COL0) - (x0 - OFF));
     const unsigned win_bytes = (unsigned)(win_elems * (int)sizeof(S));
-    const int nsrc = (y1 - y0) + 4;        // source rows y0 - 2 .. y1 + 1
+    const int npull = (y1 - y0) + 2;       // pulled rows y0 - 1 .. y1: sequence numbers 0 .. npull - 1
 
     if (t == 0) {
-        for (int s = 0; s < kTmaSlots; ++s) mbar_init(&bars[s], 1);
+        for (int q = 0; q < D; ++q) mbar_init(&bars[q], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
 
-    // source row sequence number sq (row y0 - 2 + sq) lives in slot sq % S;
-    // its k-th fill completes phase k & 1 of that slot's mbarrier
+    // warp 0 issues the pulled rows sq = issued .. last; lane q < 18 copies
+    // plane q of source row (y0 - 1 + sq) - c_qy into slot sq % D
     int issued = 0;   // meaningful in warp 0 only (all its lanes agree)
-    // warp 0: issue every sq <= last not yet issued; lane q < 18 copies plane q
-    // (the order of the arrive.expect_tx and the completions does not matter)
     auto issue_upto = [&](int last) {
-        for (; issued <= last && issued < nsrc; ++issued) {
-            const int sq = issued;
-            const int slot = sq % kTmaSlots;
-            int row = (y0 - 2 + sq) % ny;
-            if (row < 0) row += ny;
-            S* dslot = ring + (size_t)slot * TG::slot_elems;
+        for (; issued <= last && issued < npull; ++issued) {
+            const int sq = issued, slot = sq % D;
             if (t == 0) mbar_expect_tx(&bars[slot], 18u * win_bytes);
             if (t < 18) {
-                const S* g = src + (long long)row * pitch + (x0 - OFF);
-                bulk_g2s(dslot + t * WIN, g + (long long)t * plane, win_bytes, &bars[slot]);
+                int row = y0 - 1 + sq - cyo(t % 9);                            // in [-2, ny + 1]
+                row = row < 0 ? row + ny : (row >= ny ? row - ny : row);
+                row = row < 0 ? row + ny : (row >= ny ? row - ny : row);       // ny = 1
+                const S* g = src + ((unsigned)t * plane + (unsigned)(row * pitch)) + (x0 - OFF);
+                bulk_g2s(ring + (size_t)slot * TG::slot_elems + t * WIN, g, win_bytes, &bars[slot]);
             }
         }
     };
     bool timed_out = false;
     auto wait_row = [&](int sq) {
-        if (sq < nsrc && !timed_out && !mbar_wait(&bars[sq % kTmaSlots], (unsigned)((sq / kTmaSlots) & 1)))
-            timed_out = true;
+        if (!timed_out && !mbar_wait(&bars[sq % D], (unsigned)((sq / D) & 1))) timed_out = true;
     };
-    // pull of row p from source rows p - 1, p, p + 1 (sq = p - y0 + 1 .. + 3)
-    auto pull_row = [&](int p, C (&f)[2][9], unsigned& smask, int slot_d) {
-        const RowIdx q = rows_of(p, ny);
+    // pulled populations of this node in row sequence sq (row y0 - 1 + sq)
+    auto pull = [&](int sq, int rw, unsigned m, C (&f)[2][9]) {
+        const S* P = ring + (size_t)(sq % D) * TG::slot_elems + wc;
+        if (m == 0) pull_slot<S, WIN>(P, 0, cx.sh, f);
+        else pull_slot_bb<S, WIN>(P, m, cx.sh, src + (rw * pitch + xc), plane, f);
+    };
+    // densities of row sequence sq into density-ring slot `slot_d`
+    auto pull_dens = [&](int sq, unsigned& smask, int slot_d) {
+        const RowIdx q = rows_of(y0 - 1 + sq, ny);
         C nA = C(0), nB = C(0);
         smask = 0;
         if (dcol) {
             smask = nbr_solid(geo, xm, xc, xp, q.rm, q.rw, q.rp);
             if (!SOL(smask, 0, 0)) {
-                const int sqm = p - y0 + 1;
-                const S* Rm = ring + (size_t)(sqm % kTmaSlots) * TG::slot_elems + wc;
-                const S* R0 = ring + (size_t)((sqm + 1) % kTmaSlots) * TG::slot_elems + wc;
-                const S* Rp = ring + (size_t)((sqm + 2) % kTmaSlots) * TG::slot_elems + wc;
-                const unsigned m = smask;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int b = k * 9 * WIN;
-                    f[k][0] = dec(R0[b + 0 * WIN], cx.sh.v[k][0]);
-                    f[k][1] = dec(SOL(m, 0, -1) ? R0[b + 3 * WIN] : R0[b + 1 * WIN - 1], cx.sh.v[k][1]);
-                    f[k][2] = dec(SOL(m, -1, 0) ? R0[b + 4 * WIN] : Rm[b + 2 * WIN], cx.sh.v[k][1]);
-                    f[k][3] = dec(SOL(m, 0, 1) ? R0[b + 1 * WIN] : R0[b + 3 * WIN + 1], cx.sh.v[k][1]);
-                    f[k][4] = dec(SOL(m, 1, 0) ? R0[b + 2 * WIN] : Rp[b + 4 * WIN], cx.sh.v[k][1]);
-                    f[k][5] = dec(SOL(m, -1, -1) ? R0[b + 7 * WIN] : Rm[b + 5 * WIN - 1], cx.sh.v[k][2]);
-                    f[k][6] = dec(SOL(m, -1, 1) ? R0[b + 8 * WIN] : Rm[b + 6 * WIN + 1], cx.sh.v[k][2]);
-                    f[k][7] = dec(SOL(m, 1, 1) ? R0[b + 5 * WIN] : Rp[b + 7 * WIN + 1], cx.sh.v[k][2]);
-                    f[k][8] = dec(SOL(m, 1, -1) ? R0[b + 6 * WIN] : Rp[b + 8 * WIN - 1], cx.sh.v[k][2]);
-                }
+                C f[2][9];
+                pull(sq, q.rw, smask, f);
                 nA = dens9(f[0]);
                 nB = dens9(f[1]);
             }
@@ -1130,51 +1544,50 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
         }
     };
 
-    C fc[2][9], fn[2][9];
     unsigned smc = 0, smn = 0;
     bool abort_cta = false;
-    // prologue: fill the whole ring, then pull rows y0 - 1 and y0 (sq 0..3)
-    if (t < 32) issue_upto(kTmaSlots - 1);
-    for (int sq = 0; sq < 4; ++sq) wait_row(sq);
+    // prologue: fill the ring, then the densities of rows y0 - 1 and y0
+    if (t < 32) issue_upto(D - 1);
+    wait_row(0);
+    wait_row(1);
     if (!timed_out) {
-        pull_row(y0 - 1, fn, smn, 0);
-        pull_row(y0, fc, smc, 1);
+        pull_dens(0, smn, 0);
+        pull_dens(1, smc, 1);
     }
-    // the prologue pulls must be done before thread 0 refills their slots
-    if (__syncthreads_or(timed_out)) abort_cta = true;
-    for (int r = y0; r < y1 && !abort_cta; ++r) {
+    for (int r = y0; r < y1; ++r) {
+        const int sq = r - y0 + 1;   // sequence number of row r
         const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
-        // every thread finished the pulls that read source rows <= r - y0 + 1
-        // (previous barrier): refill their slots up to two rows past the next need
-        if (t < 32) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            issue_upto(r - y0 + 6);
-        }
-        wait_row(r - y0 + 4);
-        if (!timed_out) pull_row(r + 1, fn, smn, s_p);
+        wait_row(sq + 1);
+        if (!timed_out) pull_dens(sq + 1, smn, s_p);
+        // past this barrier every thread is done with the collision of row
+        // r - 1 (slot of sq - 1) and with the densities of rows up to r + 1
         if (__syncthreads_or(timed_out)) {
             abort_cta = true;
             break;
         }
+        if (t < 32) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue_upto(sq - 1 + D);
+        }
         if (coll && !SOL(smc, 0, 0)) {
-            const RowIdx q = rows_of(r, ny);
-            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, sdc, dst, plane, (unsigned)(q.rw * pitch + xc),
+            const int rw = rows_of(r, ny).rw;
+            C fc[2][9];
+            pull(sq, rw, smc, fc);
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, sdc, dst, plane, (unsigned)(rw * pitch + xc),
                                   MomOut{nullptr, nullptr, 0}, 0, ghost_r(xc, nx), ghost_l(xc, nx));
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
         smc = smn;
     }
+    // a timeout in the prologue, or in a row after the last barrier, still
+    // reaches every thread here
+    if (!abort_cta && __syncthreads_or(timed_out)) abort_cta = true;
     if (abort_cta && t == 0) {
         // drain the copies this CTA issued before it exits (bounded): the last
         // fill of each slot completes after every earlier one
-        for (int sq = max(0, issued - kTmaSlots); sq < issued; ++sq)
-            mbar_wait(&bars[sq % kTmaSlots], (unsigned)((sq / kTmaSlots) & 1));
+        for (int sq = max(0, issued - D); sq < issued; ++sq) mbar_wait(&bars[sq % D], (unsigned)((sq / D) & 1));
         atomicOr(err, ERR_TIMEOUT);
     }
-    // without a timeout every issued row (sq < nsrc) was waited on by the loop
+    // without a timeout every issued row (sq < npull) was waited on above
 }
 
 template <typename S, int W, int D>

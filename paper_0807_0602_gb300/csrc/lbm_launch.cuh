@@ -67,29 +67,38 @@ cudaError_t Launch<S>::step_async(int W, int D, const RunDesc* d_runs, const Til
     }
 }
 
-template <typename S, int W>
+template <typename S, int W, int D>
 static cudaError_t launch_tma(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, uint32_t* err,
                               cudaStream_t s) {
-    constexpr size_t smem = TmaGeom<S, W>::smem_bytes();
-    static bool configured = false;   // attribute set once per process and instantiation
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_step_tma<S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
+    constexpr size_t smem = TmaGeom<S, W, D>::smem_bytes();
+    if constexpr (smem > kMaxSmemPerCta) {
+        return cudaErrorInvalidValue;
+    } else {
+        static bool configured = false;   // attribute set once per process and instantiation
+        if (!configured) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_step_tma<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        k_step_tma<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
+        return cudaGetLastError();
     }
-    k_step_tma<S, W><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
-    return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t Launch<S>::step_tma(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+cudaError_t Launch<S>::step_tma(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                 uint32_t* err, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    switch (W) {
-        case 64: return launch_tma<S, 64>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 128: return launch_tma<S, 128>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 256: return launch_tma<S, 256>(d_runs, d_tiles, ntiles, parity, err, s);
+    switch (W * 10 + D) {
+        case 644: return launch_tma<S, 64, 4>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 646: return launch_tma<S, 64, 6>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 648: return launch_tma<S, 64, 8>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1284: return launch_tma<S, 128, 4>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1286: return launch_tma<S, 128, 6>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1288: return launch_tma<S, 128, 8>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 2564: return launch_tma<S, 256, 4>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 2566: return launch_tma<S, 256, 6>(d_runs, d_tiles, ntiles, parity, err, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -129,6 +138,53 @@ cudaError_t Launch<S>::step_l2pf(int W, const RunDesc* d_runs, const Tile* d_til
         case 64: k_step<S, 64, 0, true><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
         case 128: k_step<S, 128, 0, true><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
         case 256: k_step<S, 256, 0, true><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_smem(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step_smem<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128: k_step_smem<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 256:
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else k_step_smem<S, 256><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_pair(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step_pair<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128:
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else k_step_pair<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                 cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    // R = collided rows per tile: TY = R + 2 thread rows
+    switch (W * 100 + R) {
+        case 3206: k_step_tile<S, 32, 8><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 3214: k_step_tile<S, 32, 16><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 3230: k_step_tile<S, 32, 32><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 6406: k_step_tile<S, 64, 8><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 6414: k_step_tile<S, 64, 16><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -105,7 +105,10 @@ class Lattice:
         if isinstance(runs, dict):
             runs = [runs]
         self.runs = list(runs)
-        opt = self._options(self.runs[0]["params"], log_every, log_capacity, autotune, tile, graph_chunk, rho_ref)
+        # with an explicit kernel the tiling is set together with it after creation
+        # (the creation options only know the default kernel's tilings)
+        opt = self._options(self.runs[0]["params"], log_every, log_capacity, autotune,
+                            tile if kernel is None else (0, 0), graph_chunk, rho_ref)
         keep = []
         geoms = (L.Geometry * len(self.runs))(*[_geometry(r, keep) for r in self.runs])
         n = len(self.runs)
@@ -119,7 +122,11 @@ class Lattice:
                     "lbm_create_batch")
         self._finish_init()
         if kernel is not None:   # (kernel, depth)
-            self.schedule = (int(tile[0]), int(tile[1]), int(kernel[0]), int(kernel[1]))
+            try:
+                self.schedule = (int(tile[0]), int(tile[1]), int(kernel[0]), int(kernel[1]))
+            except Exception:
+                self.close()
+                raise
 
     def _options(self, prm, log_every, log_capacity, autotune, tile, graph_chunk, rho_ref) -> L.Options:
         opt = L.Options()
@@ -196,7 +203,10 @@ class Lattice:
 
     @property
     def schedule(self):
-        """(tile_w, tile_h, kernel, depth); kernel 0 = register pull, 1 = cp.async stages."""
+        """(tile_w, tile_h, kernel, depth); kernel is one of the LBM_KERNEL_*
+        variants of include/lbm.h (0 register pull, 1 cp.async stages, 2 TMA
+        ring, 3 pipelined, 4 species split, 5 L2 prefetch, 6 shared-memory
+        staged)."""
         v = [ctypes.c_int() for _ in range(4)]
         L.check(self._lib.lbm_get_schedule(self._h, *[ctypes.byref(x) for x in v]), "lbm_get_schedule")
         return tuple(int(x.value) for x in v)

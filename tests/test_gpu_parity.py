@@ -134,9 +134,20 @@ def test_results_independent_of_tiling_and_graphs(prec):
     if prec != "f16s":
         scheds += [((128, 16), 0, (1, 4)), ((64, 5), -1, (1, 3)), ((256, 8), 3, (1, 4)), ((64, 40), 0, (1, 4))]
     scheds += [((128, 16), 0, (2, 4)), ((64, 1), -1, (2, 4)), ((256, 7), 5, (2, 4)), ((64, 37), 0, (2, 4))]
+    scheds += [((128, 16), 0, (2, 6)), ((64, 5), -1, (2, 8)), ((128, 3), 5, (2, 8))]
+    if prec != "f64":   # FP64 at W = 256, depth 6 needs more than 227 KB of shared memory: rejected
+        scheds += [((256, 3), 5, (2, 6))]
     scheds += [((128, 16), 0, (3, 4)), ((64, 1), -1, (3, 4)), ((256, 9), 5, (3, 4)), ((64, 37), 0, (3, 4))]
     scheds += [((128, 16), 0, (4, 4)), ((64, 1), -1, (4, 4)), ((256, 9), 5, (4, 4)), ((64, 37), 0, (4, 4))]
     scheds += [((128, 16), 0, (5, 4)), ((64, 1), -1, (5, 4)), ((256, 9), 5, (5, 4)), ((64, 37), 0, (5, 4))]
+    scheds += [((128, 16), 0, (6, 4)), ((64, 1), -1, (6, 4)), ((128, 9), 5, (6, 4)), ((64, 37), 0, (6, 4))]
+    if prec != "f64":   # FP64 at W = 256 exceeds that kernel's static shared memory and is rejected
+        scheds += [((256, 9), 5, (6, 4))]
+    scheds += [((64, 16), 0, (7, 4)), ((64, 1), -1, (7, 4)), ((64, 9), 5, (7, 4)), ((64, 37), 0, (7, 4))]
+    if prec != "f64":   # the pair kernel takes W <= 64 in FP64
+        scheds += [((128, 7), 5, (7, 4)), ((128, 37), 0, (7, 4))]
+    scheds += [((32, 14), 0, (8, 4)), ((32, 6), -1, (8, 4)), ((64, 6), 5, (8, 4)), ((32, 30), 0, (8, 4)),
+               ((64, 14), 7, (8, 4))]
     outs = []
     for tile, chunk, kern in scheds:
         with Lattice(run, precision=prec, tile=tile, graph_chunk=chunk, rho_ref=(1.0, 1.0), kernel=kern) as lat:
@@ -150,10 +161,20 @@ def test_results_independent_of_tiling_and_graphs(prec):
 
 @pytest.mark.parametrize("name", ["capillary64x18", "odd17x9", "tiny5x4", "wide300x5", "box16x8"])
 @pytest.mark.parametrize("tile", [(64, 3), (128, 16), (256, 40)])
-@pytest.mark.parametrize("kernel", [2, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [2, 3, 4, 5, 6, 7, 8])
 def test_tma_pipelined_split_kernels_fp64_match_oracle(name, tile, kernel):
     geom, prm, kind = CASES[name]
     nA, nB = _fields(geom, kind)
+    if kernel == 8:   # the tile kernel's shapes: W x (R + 2) threads
+        tile = {(64, 3): (32, 6), (128, 16): (32, 14), (256, 40): (64, 14)}[tile]
+    wmax = {6: 128, 7: 64}.get(kernel, 256)   # FP64 static shared memory bounds W
+    if tile[0] > wmax:
+        from paper_0807_0602_gb300 import _lib as L
+        with pytest.raises(L.LbmError) as e:
+            Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=tile,
+                    kernel=(kernel, 4))
+        assert e.value.code == L.LBM_EINVAL
+        tile = (wmax, tile[1])
     ref = oracle.OracleLattice(geom, prm, nA, nB)
     ref.step(30)
     with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=tile,
@@ -163,14 +184,29 @@ def test_tma_pipelined_split_kernels_fp64_match_oracle(name, tile, kernel):
     assert np.array_equal(F, ref.populations())
 
 
-def test_tma_kernel_rejected_below_four_columns():
+@pytest.mark.parametrize("kernel", [2, 7, 8])
+def test_ghost_column_kernels_rejected_below_four_columns(kernel):
     from paper_0807_0602_gb300 import _lib as L
     geom, prm, kind = CASES["row3x1"]
     nA, nB = _fields(geom, kind)
     with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f32") as lat:
         with pytest.raises(L.LbmError) as e:
-            lat.schedule = (128, 16, 2, 4)
+            lat.schedule = (32, 14, kernel, 4) if kernel == 8 else (64, 16, kernel, 4)
         assert e.value.code == L.LBM_EINVAL
+
+
+@pytest.mark.parametrize("depth", [6, 8])
+@pytest.mark.parametrize("name", ["capillary64x18", "odd17x9"])
+def test_tma_ring_depths_fp64_match_oracle(name, depth):
+    geom, prm, kind = CASES[name]
+    nA, nB = _fields(geom, kind)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(30)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=(64, 7),
+                 kernel=(2, depth)) as lat:
+        lat.step(30)
+        F = lat.populations()
+    assert np.array_equal(F, ref.populations())
 
 
 def test_async_kernel_fp64_matches_oracle():
