@@ -9,7 +9,10 @@ on every 50th step the front reduction and the mass sums.
 
 value     GLUPS (lattice node updates of both species per second, all nodes),
           device time of the timed steps (CUDA events on the library's stream),
-          with L2 flushed between timed steps.
+          with L2 flushed between timed steps: a 256 MB buffer is written and
+          another 256 MB buffer read before every step, outside the timed
+          region, so the step starts with none of its data in L2 and no dirty
+          flush lines left to write back inside its own time.
 e2e       the same metric for the whole job through the C ABI with host
           buffers: initial fields uploaded from pinned host memory, the steps,
           the log and the final densities copied back, inside the timed region.
@@ -40,7 +43,12 @@ METRIC = "2-species D2Q9 GLUPS & HBM-peak fraction; FP32/batched vs FP64 at stat
 WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 populations, "
             "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
 BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
-PROFILE = os.path.join(ROOT, "profiles", "k_step_f32_capillary_8192x160.txt")
+KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
+           "node-tile"]
+KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
+                "k_step_smem", "k_step_pair", "k_step_tile"]
+# committed ncu summaries of the step kernel on this workload, by kernel variant
+PROFILES = {6: os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
                   for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "lbm_device.h")]
 
@@ -59,17 +67,20 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """DRAM bytes per step-kernel launch from the committed ncu summary, or
-    None if the kernel sources changed since the counters were taken."""
+def read_traffic(kvar: int, tile):
+    """DRAM bytes per step-kernel launch from the committed ncu summary of
+    this kernel variant and tile, or None if there is none or the kernel
+    sources changed since the counters were taken."""
+    if kvar not in PROFILES:
+        return None
     try:
         kv = {}
-        with open(PROFILE) as fh:
+        with open(PROFILES[kvar]) as fh:
             for line in fh:
                 if ":" in line:
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_hash") != kernel_hash():
+        if kv.get("kernel_hash") != kernel_hash() or kv.get("tile") != f"{tile[0]}x{tile[1]}":
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -205,7 +216,7 @@ def measure_batched(world: int, rank: int, stream, precision: str = "f32", steps
     total_nodes = nodes * world if world > 1 else nodes
     return {"value": total_nodes / (ms * 1e-3) / 1e9, "unit": "GLUPS", "runs": len(allruns),
             "nodes": total_nodes, "ms_per_step": ms, "precision": precision,
-            "schedule": {"tile": list(sched[:2]), "kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair", "node-tile"][sched[2]]},
+            "schedule": {"tile": list(sched[:2]), "kernel": KERNELS[sched[2]]},
             "runs_per_hour_at_2e4_steps": len(allruns) * 3600.0 / (ms * 1e-3 * 2e4),
             "alg_GBs": nodes * world * BYTES_PER_NODE[precision] / (ms * 1e-3) / 1e9 if world > 1 else
             nodes * BYTES_PER_NODE[precision] / (ms * 1e-3) / 1e9,
@@ -281,8 +292,9 @@ def run_profile(args):
     build_lib()
     c = workload()
     w, h, k, d = (int(v) for v in args.schedule.split(","))
+    # the z(t) and mass log every 50 steps as in the timed run
     with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision=args.precision, tile=(w, h),
-                 kernel=(k, d), graph_chunk=-1) as lat:
+                 kernel=(k, d), graph_chunk=-1, log_every=50, log_capacity=4096) as lat:
         lat.step(args.profile)
         lat.sync()
     torch.cuda.synchronize()
@@ -301,7 +313,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-run ensemble measurement")
     ap.add_argument("--profile", type=int, default=0,
                     help="only step the workload this many times (for ncu captures) and exit")
-    ap.add_argument("--schedule", default="128,16,0,4",
+    ap.add_argument("--schedule", default="128,4,6,4",
                     help="tile_w,tile_h,kernel,depth used by --profile")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -337,7 +349,9 @@ def main():
         lat.step(600)          # autotuning: real steps, every schedule gives the same bits
         lat.step(args.warmup)
         lat.sync()
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
+        flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
+        flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        flush_acc = torch.empty((), dtype=torch.float32, device=dev)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         logged = []
@@ -348,7 +362,8 @@ def main():
         barrier(world)
         torch.cuda.synchronize()
         for k in range(args.steps):
-            flush.zero_()
+            flush_w.zero_()                               # evicts the step's data from L2 ...
+            torch.sum(flush_r, 0, out=flush_acc)          # ... and leaves L2 holding clean lines
             starts[k].record(stream)
             lat.step(1)
             ends[k].record(stream)
@@ -368,7 +383,7 @@ def main():
     total_ms = max_over_ranks(world, total_ms)
     value = world * nodes * args.steps / (total_ms * 1e-3) / 1e9
     n_logs = sum(logged)
-    gpu_launches = args.steps + 4 * n_logs  # step kernel + (track, mass rows, mass final, log advance)
+    gpu_launches = args.steps + 5 * n_logs  # step kernel + (front scan, front final, mass rows, mass final, log advance)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     nA0, nB0 = W.initial_fields(c)
@@ -398,9 +413,10 @@ def main():
     peak, peak_kind = peaks()
     alg_bytes = fluid_nodes * BYTES_PER_NODE[args.precision]
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    traffic = read_traffic() if args.precision == "f32" else None
+    traffic = read_traffic(sched[2], sched[:2]) if args.precision == "f32" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind, "kernel": "k_step",
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": f"{KERNEL_NAMES[sched[2]]} (tile {sched[0]}x{sched[1]})",
                 "alg_bytes_per_launch": alg_bytes, "kernel_ms": kernel_ms}
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
@@ -408,8 +424,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [g["nx"], g["ny"]], "fluid_nodes": fluid_nodes,
                    "precision": args.precision, "tile": list(sched[:2]),
-                   "step_kernel": ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair", "node-tile"][sched[2]], "log_every": log_every,
-                   "l2": "flushed (256 MB write) between timed steps", "state_finite": finite,
+                   "step_kernel": KERNELS[sched[2]], "log_every": log_every,
+                   "l2": "flushed between timed steps: 256 MB written, then another 256 MB read",
+                   "state_finite": finite,
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "e2e": e2e,

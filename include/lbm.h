@@ -110,7 +110,10 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  *               lbm_step and keep the fastest.  Tilings change only the
  *               schedule: results are bit-identical for every tiling.
  * tile_w        CTA width (64, 128 or 256 threads; 0 = default 128);
- * tile_h        rows marched per CTA (0 = default 16, clamped to ny).
+ * tile_h        rows marched per CTA (0 = default 4, clamped to ny).
+ *               The step kernel starts as LBM_KERNEL_SMEM where it takes the
+ *               tiling (else LBM_KERNEL_REGISTER); autotune or
+ *               lbm_set_schedule change it.
  * graph_chunk   steps captured per CUDA graph when the log is off (0 = 64;
  *               -1 = launch every step directly).
  * rho_ref       FP16S shift per species (ignored otherwise).
@@ -236,8 +239,9 @@ int lbm_populations(lbm_t* h, int run, void* out, int on_device);
 /* Tiling in use (CTA width, rows per CTA). */
 int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h);
 
-/* Selects a tiling (tile_w in {64,128,256}, tile_h >= 1).  Results do not
- * depend on it. */
+/* Selects a tiling (tile_w in {64,128,256}, tile_h >= 1) for the current step
+ * kernel, or with the register kernel (LBM_KERNEL_REGISTER) if the current
+ * kernel does not take that tiling.  Results do not depend on it. */
 int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 
 /* Full schedule of the step kernel: tiling plus the kernel variant

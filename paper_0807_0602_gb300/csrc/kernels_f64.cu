@@ -11,7 +11,7 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const RunDesc* __re
                                                              uint32_t* __restrict__ err) {
     const RunDesc& rd = runs[blockIdx.x];
     __shared__ double tot[2];
-    mass_rows_total(rd.ny, partials + 2 * rd.row0, tot);
+    mass_rows_total(rd.ny * kMassChunks, partials + 2 * (long long)rd.row0 * kMassChunks, tot);
     if (threadIdx.x == 0) {
         const double MA = tot[0], MB = tot[1];
         if (mass) {

@@ -42,19 +42,20 @@ struct lbm_s {
     Tile* d_tiles = nullptr;
     size_t d_tiles_cap = 0;
     std::vector<int> tile_begin, tile_count;
-    int tile_w = 128, tile_h = 16;
-    int kvar = 0, depth = 4;       // step kernel: 0 register pull, 1 cp.async stages of depth D, 2 TMA ring,
-                                   // 3 register pull with the next row's loads in flight,
-                                   // 4 species split over two threads per node,
-                                   // 5 register pull with bulk L2 prefetch of rows ahead,
-                                   // 6 register pull with the pulled rows parked in shared memory,
-                                   // 7 two columns per thread with vector loads and stores,
-                                   // 8 one node per thread over a W x (R + 2) tile
+    int tile_w = 128, tile_h = 4;
+    int kvar = 6, depth = 4;       // step kernel (LBM_KERNEL_* of lbm.h): 0 register pull, 1 cp.async
+                                   // stages of depth D, 2 TMA ring of D row slots, 3 staged pull with the
+                                   // loads of row r + 2 in flight, 4 species split over two threads per
+                                   // node, 5 register pull with bulk L2 prefetch of rows ahead, 6 register
+                                   // pull with the pulled rows parked in shared memory, 7 two columns per
+                                   // thread, 8 one node per thread over a W x (R + 2) tile
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
     double* d_mass = nullptr;
     double* d_zout = nullptr;
+    int* d_first = nullptr;        // first failing column of each tracked row (4 per run)
+    int track_cap = 0;             // longest capillary among the runs (columns the front scan covers)
     double* d_log = nullptr;
     long long* d_logcount = nullptr;
     uint32_t* d_err = nullptr;
@@ -245,6 +246,8 @@ bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
     // the shared-memory-staged kernel keeps 18 W populations per row parity in
     // static shared memory: FP64 at W = 256 would exceed the 48 KB static limit
     if (kvar == 6 && h->precision == LBM_F64 && W == 256) return false;
+    // the pipelined kernel stages three rows of 18 W populations statically
+    if (kvar == 3 && (W > 128 || (h->precision == LBM_F64 && W > 64))) return false;
     if (kvar == 7) {
         // two columns per thread: 2W columns of staged populations per CTA
         // (W <= 128, FP64 W = 64); pulls read the ghost columns: nx >= 4
@@ -270,7 +273,9 @@ bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
 // Issues the log sequence for the state in buffer `parity`.
 cudaError_t issue_log(lbm_t* h, int parity, cudaStream_t s) {
     sc::LogCtl lc = logctl(h);
-    cudaError_t e = dispatch(h->precision, [&](auto L) { return L.track(h->d_runs, h->nruns, parity, lc, nullptr, s); });
+    cudaError_t e = dispatch(h->precision, [&](auto L) {
+        return L.track(h->d_runs, h->nruns, h->track_cap, parity, h->d_first, lc, nullptr, s);
+    });
     if (e != cudaSuccess) return e;
     e = dispatch(h->precision, [&](auto L) {
         return L.mass(h->d_runs, h->nruns, h->d_rows, (int)h->rows.size(), parity, h->d_partials, nullptr, lc, 1,
@@ -346,26 +351,19 @@ int autotune(lbm_t* h, int64_t* n) {
     };
     int maxny = 1;
     for (auto& rd : h->runs) maxny = std::max(maxny, rd.ny);
-    std::vector<int> Rs = {8, 16, 32};
+    std::vector<int> Rs = {4, 8, 16, 32};
     if (maxny < 32) Rs.push_back(maxny);
-    else Rs.push_back(64);
     std::sort(Rs.begin(), Rs.end());
     Rs.erase(std::unique(Rs.begin(), Rs.end()), Rs.end());
+    // the variants that have been competitive somewhere; the cp.async and
+    // species-split kernels stay selectable by lbm_set_schedule
     std::vector<Cand> cands;
     for (int W : {64, 128, 256})
-        for (int R : Rs) {
-            cands.push_back({W, R, 0, 4});
-            cands.push_back({W, R, 3, 4});
-            cands.push_back({W, R, 4, 4});
-            cands.push_back({W, R, 5, 4});
-            if (schedule_ok(h, W, R, 6, 4)) cands.push_back({W, R, 6, 4});
-            if (schedule_ok(h, W, R, 7, 4)) cands.push_back({W, R, 7, 4});
-            for (int D : {4, 6, 8})
-                if (schedule_ok(h, W, R, 2, D)) cands.push_back({W, R, 2, D});
-            if (W < 256 && schedule_ok(h, W, R, 1, 4)) cands.push_back({W, R, 1, 4});
-        }
+        for (int R : Rs)
+            for (int kvar : {6, 0, 5, 3, 7, 2})
+                if (schedule_ok(h, W, R, kvar, 4)) cands.push_back({W, R, kvar, 4});
     for (int W : {32, 64})
-        for (int R : {6, 14, 30})
+        for (int R : {6, 14})
             if (schedule_ok(h, W, R, 8, 4)) cands.push_back({W, R, 8, 4});
     const int per = 6;
     if (*n < (int64_t)cands.size() * (per + 1)) return LBM_OK;  // too short to tune now
@@ -546,12 +544,17 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
     }
     h->d_logcount = static_cast<long long*>(dalloc(h, sizeof(long long)));
     h->d_err = static_cast<uint32_t*>(dalloc(h, sizeof(uint32_t)));
-    h->d_partials = static_cast<double*>(dalloc(h, (size_t)2 * h->rows.size() * sizeof(double)));
+    h->d_partials = static_cast<double*>(dalloc(h, (size_t)2 * sc::kMassChunks * h->rows.size() * sizeof(double)));
     h->d_mass = static_cast<double*>(dalloc(h, (size_t)2 * n * sizeof(double)));
     h->d_zout = static_cast<double*>(dalloc(h, (size_t)3 * n * sizeof(double)));
+    h->d_first = static_cast<int*>(dalloc(h, (size_t)4 * n * sizeof(int)));
+    for (const RunDesc& rd : h->runs)
+        if (rd.y_bot >= 0 && rd.y_top >= 0 && rd.y_top - rd.y_bot >= 2 && rd.cap_x1 > rd.cap_x0)
+            h->track_cap = std::max(h->track_cap, rd.cap_x1 - rd.cap_x0);
     h->d_rows = static_cast<int2*>(dalloc(h, h->rows.size() * sizeof(int2)));
     h->d_runs = static_cast<RunDesc*>(dalloc(h, (size_t)n * sizeof(RunDesc)));
-    if (!h->d_logcount || !h->d_err || !h->d_partials || !h->d_mass || !h->d_zout || !h->d_rows || !h->d_runs)
+    if (!h->d_logcount || !h->d_err || !h->d_partials || !h->d_mass || !h->d_zout || !h->d_first || !h->d_rows ||
+        !h->d_runs)
         return fail(LBM_ENOMEM);
     if (cudaMemsetAsync(h->d_logcount, 0, sizeof(long long), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream) != cudaSuccess ||
@@ -565,7 +568,11 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
     // the host vectors above were read by async copies from pageable memory
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     const int W = opt.tile_w ? opt.tile_w : 128;
-    const int R = opt.tile_h ? opt.tile_h : 16;
+    const int R = opt.tile_h ? opt.tile_h : 4;
+    // default kernel: the shared-memory-staged march, or the register march
+    // for tilings it does not take
+    h->kvar = schedule_ok(h, W, R, 6, 4) ? 6 : 0;
+    h->depth = 4;
     if ((rc = upload_tiles(h, W, R))) return fail(rc);
     if (opt.log_every > 0) {
         e = issue_log(h, 0, h->stream);
@@ -626,7 +633,7 @@ void lbm_default_options(lbm_options* opt) {
     opt->log_capacity = 0;
     opt->autotune = 0;
     opt->tile_w = 128;
-    opt->tile_h = 16;
+    opt->tile_h = 4;
     opt->graph_chunk = 0;
     opt->rho_bulk = 2.0;
 }
@@ -693,7 +700,7 @@ int lbm_interface_positions(lbm_t* h, int run, double* z_bulk, double z_prec[2])
     if (rd.y_bot < 0 || rd.y_top < 0 || rd.y_top - rd.y_bot < 2 || rd.cap_x1 <= rd.cap_x0) return LBM_ESTATE;
     sc::LogCtl lc{nullptr, 1, 0};
     cudaError_t e = dispatch(h->precision, [&](auto L) {
-        return L.track(h->d_runs, h->nruns, (int)(h->t & 1), lc, h->d_zout, h->stream);
+        return L.track(h->d_runs, h->nruns, h->track_cap, (int)(h->t & 1), h->d_first, lc, h->d_zout, h->stream);
     });
     if (e != cudaSuccess) return cuda_fail(h, e);
     double z[3];
@@ -774,7 +781,13 @@ int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h) {
 }
 
 int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h) {
-    if (!h || !schedule_ok(h, tile_w, tile_h, h->kvar, h->depth)) return LBM_EINVAL;
+    if (!h) return LBM_EINVAL;
+    if (!schedule_ok(h, tile_w, tile_h, h->kvar, h->depth)) {
+        // the current kernel does not take this tiling: the register march does
+        if (!schedule_ok(h, tile_w, tile_h, 0, 4)) return LBM_EINVAL;
+        h->kvar = 0;
+        h->depth = 4;
+    }
     h->tuned = true;
     return upload_tiles(h, tile_w, tile_h);
 }

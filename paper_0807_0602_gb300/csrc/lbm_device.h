@@ -32,6 +32,9 @@ struct RunDesc {
 
 // A CTA's work: run, first collided column x0 (the CTA collides
 // min(W - 2, nx - x0) columns), rows [y0, y1).
+// column chunks (CTAs) per row of the mass reduction
+constexpr int kMassChunks = 4;
+
 // opt-in shared memory per CTA on sm_103a (227 KB)
 constexpr size_t kMaxSmemPerCta = 232448;
 
@@ -80,8 +83,8 @@ struct Launch {
                                MomOut out, cudaStream_t s);
     static cudaError_t densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA,
                                  double* nB, cudaStream_t s);
-    static cudaError_t track(const RunDesc* d_runs, int nruns, int parity, LogCtl lc, double* zout,
-                             cudaStream_t s);
+    static cudaError_t track(const RunDesc* d_runs, int nruns, int max_cap, int parity, int* first, LogCtl lc,
+                             double* zout, cudaStream_t s);
     static cudaError_t mass(const RunDesc* d_runs, int nruns, const int2* d_rows, int nrows, int parity,
                             double* d_partials, double* d_mass, LogCtl lc, int write_log, uint32_t* d_err,
                             cudaStream_t s);

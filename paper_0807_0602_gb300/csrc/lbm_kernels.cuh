@@ -1105,11 +1105,12 @@ __global__ void __launch_bounds__(W * TY, (kTileMinBlocks<S, W, TY>)) k_step_til
                              ghost_l(xw, nx));
 }
 
-// ---- software-pipelined register variant ------------------------------------
-// k_step with the loads of row r + 2 issued (into raw registers) before row
-// r + 1 is decoded and row r collided: each row's HBM latency overlaps a
-// full row of arithmetic instead of stalling it.  Same column/row march,
-// same collision, same bits.
+// ---- software-pipelined staged variant ---------------------------------------
+// k_step_smem's march with the loads of row r + 2 issued (into raw
+// registers) before row r is collided, and decoded (densities into the ring,
+// populations into a 3-row shared-memory stage) only after the collision:
+// every thread keeps a row of HBM reads in flight through the arithmetic of
+// the previous one.  Same column/row march, same collision, same bits.
 template <typename S>
 __device__ __forceinline__ void issue_pull(const S* __restrict__ src, unsigned plane, unsigned own, unsigned oxm,
                                            unsigned oxp, unsigned orm, unsigned orp, unsigned orm_xm,
@@ -1149,15 +1150,19 @@ __device__ __forceinline__ void issue_pull(const S* __restrict__ src, unsigned p
 }
 
 template <typename S, int W>
-__global__ void __launch_bounds__(W) k_step_pf(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
-                                               int parity) {
+constexpr int kPipeMinBlocks = (sizeof(typename Prec<S>::C) == 8 || W >= 768) ? 1 : 768 / W;   // <= 85 registers
+
+template <typename S, int W>
+__global__ void __launch_bounds__(W, (kPipeMinBlocks<S, W>)) k_step_pf(const RunDesc* __restrict__ runs,
+                                                                      const Tile* __restrict__ tiles, int parity) {
     using C = typename Prec<S>::C;
     __shared__ C sd[4][2][W];
+    __shared__ C ps[3][18][W];   // pulled populations of rows y0 + 3m + {0, 1, 2}: [row][population][thread]
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
-    const long long plane = rd.plane;
+    const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
@@ -1165,6 +1170,7 @@ __global__ void __launch_bounds__(W) k_step_pf(const RunDesc* __restrict__ runs,
     cx.load(rd);
     const int t = threadIdx.x;
     const StripCols sc(tl.x0, nx, W, t);
+    const int y0 = tl.y0, y1 = tl.y1;
 
     // issue the loads of row p into raw; smask = solid flags around (x, p)
     auto issue = [&](int p, S (&raw)[18], unsigned& smask) {
@@ -1180,48 +1186,60 @@ __global__ void __launch_bounds__(W) k_step_pf(const RunDesc* __restrict__ runs,
             }
         }
     };
-    // decode a pulled row and put its densities into ring slot `slot`
-    auto finish = [&](const S (&raw)[18], unsigned smask, C (&f)[2][9], int slot) {
+    // decode pulled row p: densities into ring slot `slot`, populations into
+    // ps when p is a collided row of the tile
+    auto finish = [&](int p, const S (&raw)[18], unsigned smask, int slot) {
         C nA = C(0), nB = C(0);
         if (sc.dcol && !SOL(smask, 0, 0)) {
+            C f[2][9];
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[k][i] = dec(raw[k * 9 + i], cx.sh.v[k][grp(i)]);
             nA = dens9(f[0]);
             nB = dens9(f[1]);
+            if (sc.coll && p >= y0 && p < y1) {
+                const int b = (p - y0) % 3;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) ps[b][k * 9 + i][t] = f[k][i];
+            }
         }
         sd[slot][0][t] = nA;
         sd[slot][1][t] = nB;
     };
 
-    const int y0 = tl.y0, y1 = tl.y1;
-    C fc[2][9], fn[2][9];
-    S rn[18], rn2[18];
-    unsigned smc = 0, smn = 0, smn2 = 0;
-    issue(y0 - 1, rn, smn);
-    finish(rn, smn, fn, 0);            // halo row: densities only
+    S rn[18];
+    unsigned smc = 0, smn = 0, smq = 0;
+    issue(y0 - 1, rn, smq);
+    finish(y0 - 1, rn, smq, 0);        // halo row: densities only
     issue(y0, rn, smc);
-    finish(rn, smc, fc, 1);
-    issue(y0 + 1, rn, smn);            // in flight into the loop
+    finish(y0, rn, smc, 1);
+    issue(y0 + 1, rn, smn);
+    finish(y0 + 1, rn, smn, 2);
+    __syncthreads();
     for (int r = y0; r < y1; ++r) {
-        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3;
-        if (r + 2 <= y1) issue(r + 2, rn2, smn2);
-        finish(rn, smn, fn, s_p);      // row r + 1, loaded one iteration ago
-        __syncthreads();
+        const int s_m = (r - y0) & 3, s_0 = (r - y0 + 1) & 3, s_p = (r - y0 + 2) & 3, s_n = (r - y0 + 3) & 3;
+        // the loads of row r + 2 stay in flight while row r is collided
+        const bool ahead = r + 2 <= y1;
+        if (ahead) issue(r + 2, rn, smq);
         if (sc.coll && !SOL(smc, 0, 0)) {
-            const RowIdx q = rows_of(r, ny);
-            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (unsigned)(q.rw * pitch + sc.xc),
+            const int b = (r - y0) % 3;
+            C fc[2][9];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fc[k][i] = ps[b][k * 9 + i][t];
+            const int rw = rows_of(r, ny).rw;
+            collide_any<S, W, 0>(cx, fc, smc, sd, s_m, s_0, s_p, t, dst, plane, (unsigned)(rw * pitch + sc.xc),
                                   MomOut{nullptr, nullptr, 0}, 0, ghost_r(sc.xc, nx), ghost_l(sc.xc, nx));
         }
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fc[k][i] = fn[k][i];
-#pragma unroll
-        for (int i = 0; i < 18; ++i) rn[i] = rn2[i];
+        // slot s_n held row r - 2, last read by the collision of row r - 1
+        if (ahead) finish(r + 2, rn, smq, s_n);
+        __syncthreads();
         smc = smn;
-        smn = smn2;
+        smn = smq;
     }
 }
 
@@ -1716,13 +1734,14 @@ __global__ void k_import(const RunDesc* __restrict__ runs, int run, int parity, 
 }
 
 // ---- fronts (Numerical Results section, Figs. 6-8) -------------------------
-// One CTA of 4 x 256 threads per run; group w scans tracked row w from cap_x0:
-//   w = 0, 1: the centre row(s) with v = phi = (n_A - n_B)/(n_A + n_B);
-//   w = 2, 3: the fluid rows next to the bottom / top plate with
+// Four tracked rows per run, scanned from cap_x0:
+//   g = 0, 1: the centre row(s) with v = phi = (n_A - n_B)/(n_A + n_B);
+//   g = 2, 3: the fluid rows next to the bottom / top plate with
 //             v = n_A - rho_bulk / 3.
-// Thread t of a group tests columns cap_x0 + t, + 256, ... in increasing
-// order and keeps its first failing one (v < 0); a shared atomicMin gives the
-// first failing column x* of the row (order-free, so deterministic).  Then
+// The scan gives every capillary column of every tracked row its own
+// thread; a thread whose column fails (v < 0) takes part in an atomicMin, so
+// first[4 run + g] ends as the first failing column x* whatever the order
+// (deterministic).  The finishing kernel then interpolates
 // z = (x* - 1 - cap_x0) + v(x* - 1) / (v(x* - 1) - v(x*)) in FP64.
 template <typename S>
 __device__ __forceinline__ double front_value(const RunDesc& rd, const S* base, const Shift<S>& sh, int x,
@@ -1734,95 +1753,149 @@ __device__ __forceinline__ double front_value(const RunDesc& rd, const S* base, 
     return __ddiv_rn(__dsub_rn(a, b), __dadd_rn(a, b));
 }
 
-constexpr int kTrackGroup = 256;
+// Whether the run has a channel to track, and tracked row g of it.
+__device__ __forceinline__ bool track_has(const RunDesc& rd) {
+    return rd.y_bot >= 0 && rd.y_top >= 0 && rd.y_top - rd.y_bot >= 2 && rd.cap_x1 > rd.cap_x0;
+}
+__device__ __forceinline__ int track_row(const RunDesc& rd, int g) {
+    const int H = rd.y_top - rd.y_bot - 1;
+    if (g == 0) return (H % 2 == 0) ? rd.y_bot + H / 2 : rd.y_bot + (H + 1) / 2;
+    if (g == 1) return (H % 2 == 0) ? rd.y_bot + H / 2 + 1 : rd.y_bot + (H + 1) / 2;
+    return g == 2 ? rd.y_bot + 1 : rd.y_top - 1;
+}
 
+constexpr int kTrackThreads = 256;
+constexpr int kNoFront = 0x7f7f7f7f;   // "no failing column" (the byte pattern first[] is reset to)
+
+// grid (column chunks of kTrackThreads, runs); first[] preset to kNoFront
 template <typename S>
-__global__ void __launch_bounds__(4 * kTrackGroup) k_track(const RunDesc* __restrict__ runs, int parity, LogCtl lc,
-                                                          double* __restrict__ zout) {
-    const RunDesc& rd = runs[blockIdx.x];
-    __shared__ double zr[4];
-    __shared__ int first[4];
-    const int grp_id = threadIdx.x / kTrackGroup, lt = threadIdx.x % kTrackGroup;
-    const bool has = rd.y_bot >= 0 && rd.y_top >= 0 && rd.y_top - rd.y_bot >= 2 && rd.cap_x1 > rd.cap_x0;
-    if (lt == 0) first[grp_id] = 0x7fffffff;
-    __syncthreads();
+__global__ void __launch_bounds__(kTrackThreads) k_track_scan(const RunDesc* __restrict__ runs, int parity,
+                                                             int* __restrict__ first) {
+    const RunDesc& rd = runs[blockIdx.y];
+    if (!track_has(rd)) return;
+    const int x = rd.cap_x0 + blockIdx.x * kTrackThreads + threadIdx.x;
+    if (x >= rd.cap_x1) return;
     Shift<S> sh;
     sh.load(rd);
     const S* base = static_cast<const S*>(rd.buf[parity]);
-    int y = 0;
-    const bool prec = grp_id >= 2;
-    if (has) {
-        const int H = rd.y_top - rd.y_bot - 1;
-        if (grp_id == 0) y = (H % 2 == 0) ? rd.y_bot + H / 2 : rd.y_bot + (H + 1) / 2;
-        else if (grp_id == 1) y = (H % 2 == 0) ? rd.y_bot + H / 2 + 1 : rd.y_bot + (H + 1) / 2;
-        else if (grp_id == 2) y = rd.y_bot + 1;
-        else y = rd.y_top - 1;
-        for (int x = rd.cap_x0 + lt; x < rd.cap_x1; x += kTrackGroup)
-            if (front_value<S>(rd, base, sh, x, y, prec) < 0.0) {
-                atomicMin(&first[grp_id], x);
-                break;
-            }
-    }
-    __syncthreads();
-    if (lt == 0) {
-        double z;
-        if (!has) {
-            z = __longlong_as_double(0x7ff8000000000000LL);  // NaN: no channel
-        } else if (first[grp_id] == 0x7fffffff) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        if (front_value<S>(rd, base, sh, x, track_row(rd, g), g >= 2) < 0.0) atomicMin(&first[4 * blockIdx.y + g], x);
+}
+
+// one warp per run: lanes 0-3 interpolate their row's front, lane 0 writes
+template <typename S>
+__global__ void __launch_bounds__(32) k_track_final(const RunDesc* __restrict__ runs, int parity,
+                                                   const int* __restrict__ first, LogCtl lc,
+                                                   double* __restrict__ zout) {
+    const RunDesc& rd = runs[blockIdx.x];
+    const int g = threadIdx.x;
+    const bool has = track_has(rd);
+    double z = __longlong_as_double(0x7ff8000000000000LL);   // NaN: no channel
+    if (g < 4 && has) {
+        Shift<S> sh;
+        sh.load(rd);
+        const S* base = static_cast<const S*>(rd.buf[parity]);
+        const int y = track_row(rd, g);
+        const bool prec = g >= 2;
+        const int found = first[4 * blockIdx.x + g];
+        if (found == kNoFront) {
             z = (double)(rd.cap_x1 - rd.cap_x0);
         } else {
-            const int found = first[grp_id];
             const int xp = found == 0 ? rd.nx - 1 : found - 1;
             const double v = front_value<S>(rd, base, sh, found, y, prec);
             const double vp = front_value<S>(rd, base, sh, xp, y, prec);
             if (!(vp >= 0.0)) z = (double)(found - rd.cap_x0);
             else z = __dadd_rn((double)(found - 1 - rd.cap_x0), __ddiv_rn(vp, __dsub_rn(vp, v)));
         }
-        zr[grp_id] = z;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double zb;
+    const double z0 = __shfl_sync(0xffffffffu, z, 0), z1 = __shfl_sync(0xffffffffu, z, 1);
+    const double z2 = __shfl_sync(0xffffffffu, z, 2), z3 = __shfl_sync(0xffffffffu, z, 3);
+    if (g == 0) {
+        double zb = z0;
         if (has) {
             const int H = rd.y_top - rd.y_bot - 1;
-            zb = (H % 2 == 0) ? __dmul_rn(0.5, __dadd_rn(zr[0], zr[1])) : zr[0];
-        } else {
-            zb = zr[0];
+            if (H % 2 == 0) zb = __dmul_rn(0.5, __dadd_rn(z0, z1));
         }
         if (zout) {
             zout[blockIdx.x * 3 + 0] = zb;
-            zout[blockIdx.x * 3 + 1] = zr[2];
-            zout[blockIdx.x * 3 + 2] = zr[3];
+            zout[blockIdx.x * 3 + 1] = z2;
+            zout[blockIdx.x * 3 + 2] = z3;
         }
         if (rd.log && lc.count) {
             const long long c = *lc.count;
             double* rec = rd.log + (c % lc.cap) * 6;
             rec[0] = (double)(c * (long long)lc.log_every);
             rec[1] = zb;
-            rec[2] = zr[2];
-            rec[3] = zr[3];
+            rec[2] = z2;
+            rec[3] = z3;
         }
     }
 }
 
 // ---- deterministic FP64 mass sums -----------------------------------------
-// Pass 1: one CTA of kMassThreads per (run, row): thread t sums columns t,
-// t + kMassThreads, ... in order, then a fixed shared-memory tree.  Pass 2:
-// one CTA per run sums its rows the same way.  The order never depends on
-// timing, so repeated runs give identical bits.
-constexpr int kMassThreads = 512;
+// Pass 1: kMassChunks CTAs of kMassThreads per (run, row): thread t of chunk
+// c sums columns c kMassThreads + t, then every kMassChunks kMassThreads
+// further, in order, then a fixed shared-memory tree.  Pass 2: one CTA per
+// run sums its (row, chunk) partials the same way.  The order never depends
+// on timing, so repeated runs give identical bits.
+//
+// FP64 storage sums the populations in FP64.  FP32 and FP16 storage hold
+// FP32 values: a thread accumulates them in a compensated FP32 pair (Knuth's
+// TwoSum keeps every rounding error, so hi + lo carries about 48 significant
+// bits) and enters FP64 once, at the tree; the FP64 pipe of sm_103a, a small
+// fraction of its FP32 rate, then does a few operations per thread instead
+// of two per population.
+constexpr int kMassThreads = 256;   // kMassChunks (column chunks per row) is in lbm_device.h
 
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest FP32).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+struct Sum2f {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return __dadd_rn((double)hi, (double)lo); }
+};
+
+// Sum over columns chunk * kMassThreads + t + j * nchunks * kMassThreads
+// of row y (thread t, j = 0, 1, ...), then the CTA's tree.
 template <typename S>
-__device__ __forceinline__ void mass_row_sum(const RunDesc& rd, const S* base, int y, double* out2) {
+__device__ __forceinline__ void mass_row_sum(const RunDesc& rd, const S* base, int y, int chunk, int nchunks,
+                                             double* out2) {
+    const int x_first = chunk * kMassThreads + (int)threadIdx.x, x_step = nchunks * kMassThreads;
     Shift<S> sh;
     sh.load(rd);
     const Geo geo{rd.nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const unsigned plane = (unsigned)rd.plane;
     double a = 0.0, b = 0.0;
-    for (int x = threadIdx.x; x < rd.nx; x += kMassThreads) {
-        if (geo.solid(x, y)) continue;
-        const long long o = (long long)y * rd.pitch + x;
-        a = __dadd_rn(a, node_density<S>(rd, base, sh, 0, o));
-        b = __dadd_rn(b, node_density<S>(rd, base, sh, 1, o));
+    if constexpr (sizeof(typename Prec<S>::C) == 8) {
+        for (int x = x_first; x < rd.nx; x += x_step) {
+            if (geo.solid(x, y)) continue;
+            const long long o = (long long)y * rd.pitch + x;
+            a = __dadd_rn(a, node_density<S>(rd, base, sh, 0, o));
+            b = __dadd_rn(b, node_density<S>(rd, base, sh, 1, o));
+        }
+    } else {
+        Sum2f sa, sb;
+        const S* row = base + (long long)y * rd.pitch;
+        for (int x = x_first; x < rd.nx; x += x_step) {
+            if (geo.solid(x, y)) continue;
+            const S* p = row + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sa.add(dec(ldg(p + (unsigned)i * plane), sh.v[0][grp(i)]));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sb.add(dec(ldg(p + (unsigned)(9 + i) * plane), sh.v[1][grp(i)]));
+        }
+        a = sa.value();
+        b = sb.value();
     }
     __shared__ double s[2][kMassThreads];
     s[0][threadIdx.x] = a;
@@ -1847,7 +1920,8 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_rows(const RunDesc* __res
                                                             double* __restrict__ partials) {
     const int2 ry = rows[blockIdx.x];
     const RunDesc& rd = runs[ry.x];
-    mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[parity]), ry.y, partials + 2 * blockIdx.x);
+    mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[parity]), ry.y, blockIdx.y, kMassChunks,
+                    partials + 2 * ((long long)blockIdx.x * kMassChunks + blockIdx.y));
 }
 
 // Pass 2 over the rows of one run (shared with the allocation-free variant).

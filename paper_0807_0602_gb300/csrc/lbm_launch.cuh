@@ -109,8 +109,11 @@ cudaError_t Launch<S>::step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
         case 64: k_step_pf<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 128: k_step_pf<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 256: k_step_pf<S, 256><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128:
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else k_step_pf<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
+            break;
+
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -211,10 +214,17 @@ cudaError_t Launch<S>::densities(const RunDesc* d_runs, int run, int parity, int
 }
 
 template <typename S>
-cudaError_t Launch<S>::track(const RunDesc* d_runs, int nruns, int parity, LogCtl lc, double* zout,
-                             cudaStream_t s) {
+cudaError_t Launch<S>::track(const RunDesc* d_runs, int nruns, int max_cap, int parity, int* first, LogCtl lc,
+                             double* zout, cudaStream_t s) {
     if (nruns <= 0) return cudaSuccess;
-    k_track<S><<<nruns, 4 * kTrackGroup, 0, s>>>(d_runs, parity, lc, zout);
+    cudaError_t e = cudaMemsetAsync(first, 0x7f, (size_t)4 * nruns * sizeof(int), s);   // kNoFront
+    if (e != cudaSuccess) return e;
+    if (max_cap > 0) {
+        k_track_scan<S><<<dim3((max_cap + kTrackThreads - 1) / kTrackThreads, nruns), kTrackThreads, 0, s>>>(
+            d_runs, parity, first);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_track_final<S><<<nruns, 32, 0, s>>>(d_runs, parity, first, lc, zout);
     return cudaGetLastError();
 }
 
@@ -223,7 +233,7 @@ cudaError_t Launch<S>::mass(const RunDesc* d_runs, int nruns, const int2* d_rows
                             double* d_partials, double* d_mass, LogCtl lc, int write_log, uint32_t* d_err,
                             cudaStream_t s) {
     if (nruns <= 0) return cudaSuccess;
-    k_mass_rows<S><<<nrows, kMassThreads, 0, s>>>(d_runs, d_rows, parity, d_partials);
+    k_mass_rows<S><<<dim3(nrows, kMassChunks), kMassThreads, 0, s>>>(d_runs, d_rows, parity, d_partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_mass_final<<<nruns, kMassThreads, 0, s>>>(d_runs, d_partials, d_mass, lc, write_log, d_err);

@@ -4,8 +4,10 @@
 // lbm_mass needs per-row partial sums between its two passes and keeps them
 // in device memory that lbm_create allocated.  Code that cannot allocate
 // device memory at the point where it needs the sums (see the header) gets
-// the same two passes here with the partial sums in one file-scope device
-// array of fixed size, shared by every call on a device.
+// the same per-row sum and final tree here, with the partial sums in one
+// file-scope device array of fixed size, shared by every call on a device.
+// lbm_mass splits each row into column chunks for parallelism; this variant
+// sums a whole row per CTA, so the two agree to rounding, not bit for bit.
 #include <mutex>
 
 #include "lbm.h"
@@ -24,13 +26,13 @@ static __device__ __align__(256) double g_row_sums[2 * kMaxRows];
 std::mutex g_setup_mutex;
 double* g_row_sums_addr[kMaxDevices] = {};   // device address of g_row_sums per device
 
-// Pass 1: one CTA per row, the same order as k_mass_rows.
+// Pass 1: one CTA per row (a single column chunk).
 template <typename S>
 __global__ void __launch_bounds__(sc::kMassThreads) k_rows_noalloc(sc::RunDesc rd, double* __restrict__ part) {
-    sc::mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[0]), blockIdx.x, part + 2 * blockIdx.x);
+    sc::mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[0]), blockIdx.x, 0, 1, part + 2 * blockIdx.x);
 }
 
-// Pass 2: one CTA sums the rows in the same order as k_mass_final.
+// Pass 2: one CTA sums the rows with k_mass_final's tree.
 __global__ void __launch_bounds__(sc::kMassThreads) k_final_noalloc(int ny, const double* __restrict__ part,
                                                                     double* __restrict__ mass) {
     sc::mass_rows_total(ny, part, mass);

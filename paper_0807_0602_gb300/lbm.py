@@ -82,7 +82,7 @@ class Lattice:
     """
 
     def __init__(self, runs, precision: str = "f32", log_every: int = 0, log_capacity: int = 0,
-                 autotune: bool = False, tile=(128, 16), graph_chunk: int = 0, rho_ref=(0.0, 0.0),
+                 autotune: bool = False, tile=(128, 4), graph_chunk: int = 0, rho_ref=(0.0, 0.0),
                  stream=None, torch_allocator: bool = True, kernel=None, _handle=None):
         import torch
         lib = L.load()

@@ -115,7 +115,7 @@ def test_default_options(lib):
     from paper_0807_0602_gb300 import _lib as L
     opt = L.Options()
     lib.lbm_default_options(ctypes.byref(opt))
-    assert opt.precision == L.LBM_F32 and opt.tile_w == 128 and opt.tile_h == 16 and opt.rho_bulk == 2.0
+    assert opt.precision == L.LBM_F32 and opt.tile_w == 128 and opt.tile_h == 4 and opt.rho_bulk == 2.0
 
 
 def test_structure_layouts_match_header():

@@ -137,7 +137,9 @@ def test_results_independent_of_tiling_and_graphs(prec):
     scheds += [((128, 16), 0, (2, 6)), ((64, 5), -1, (2, 8)), ((128, 3), 5, (2, 8))]
     if prec != "f64":   # FP64 at W = 256, depth 6 needs more than 227 KB of shared memory: rejected
         scheds += [((256, 3), 5, (2, 6))]
-    scheds += [((128, 16), 0, (3, 4)), ((64, 1), -1, (3, 4)), ((256, 9), 5, (3, 4)), ((64, 37), 0, (3, 4))]
+    scheds += [((64, 16), 0, (3, 4)), ((64, 1), -1, (3, 4)), ((64, 9), 5, (3, 4)), ((64, 37), 0, (3, 4))]
+    if prec != "f64":   # the pipelined kernel takes W <= 64 in FP64
+        scheds += [((128, 2), 0, (3, 4)), ((128, 9), 5, (3, 4))]
     scheds += [((128, 16), 0, (4, 4)), ((64, 1), -1, (4, 4)), ((256, 9), 5, (4, 4)), ((64, 37), 0, (4, 4))]
     scheds += [((128, 16), 0, (5, 4)), ((64, 1), -1, (5, 4)), ((256, 9), 5, (5, 4)), ((64, 37), 0, (5, 4))]
     scheds += [((128, 16), 0, (6, 4)), ((64, 1), -1, (6, 4)), ((128, 9), 5, (6, 4)), ((64, 37), 0, (6, 4))]
@@ -167,7 +169,7 @@ def test_tma_pipelined_split_kernels_fp64_match_oracle(name, tile, kernel):
     nA, nB = _fields(geom, kind)
     if kernel == 8:   # the tile kernel's shapes: W x (R + 2) threads
         tile = {(64, 3): (32, 6), (128, 16): (32, 14), (256, 40): (64, 14)}[tile]
-    wmax = {6: 128, 7: 64}.get(kernel, 256)   # FP64 static shared memory bounds W
+    wmax = {3: 64, 6: 128, 7: 64}.get(kernel, 256)   # FP64 static shared memory bounds W
     if tile[0] > wmax:
         from paper_0807_0602_gb300 import _lib as L
         with pytest.raises(L.LbmError) as e:
