@@ -261,9 +261,12 @@ def run_reference(args):
     rate = 3 * 64 * g["ny"] / (time.perf_counter() - t0)
     total = max(1, args.steps + args.warmup)
     ncols = int(max(8, min(g["nx"], rate * 90.0 / total / g["ny"])))
-    x0 = g["cap_x0"] - ncols // 4
-    sub = dict(nx=ncols, ny=g["ny"], cap_x0=g["cap_x0"] - x0, cap_x1=min(ncols, g["cap_x1"] - x0),
-               y_bot=g["y_bot"], y_top=g["y_top"])
+    if ncols >= g["nx"]:     # the whole grid fits the time budget
+        x0, ncols, sub = 0, g["nx"], dict(g)
+    else:                    # a periodic window around the inlet of the capillary
+        x0 = max(0, min(g["cap_x0"] - ncols // 4, g["nx"] - ncols))
+        sub = dict(nx=ncols, ny=g["ny"], cap_x0=max(0, g["cap_x0"] - x0), cap_x1=min(ncols, g["cap_x1"] - x0),
+                   y_bot=g["y_bot"], y_top=g["y_top"])
     sA = np.ascontiguousarray(nA[:, x0:x0 + ncols])
     sB = np.ascontiguousarray(nB[:, x0:x0 + ncols])
     o = oracle.OracleLattice(sub, c["params"], sA, sB)
@@ -273,7 +276,9 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     nodes = ncols * g["ny"]
     value = nodes * args.steps / dt / 1e9
-    sample = f"{ncols}x{g['ny']} window of the 8192x160 workload at the inlet, FP64 oracle, one host thread"
+    sample = (f"{ncols}x{g['ny']} " + ("grid (the whole workload)" if ncols == g["nx"] else
+                                        "periodic window of the 8192x160 workload at the capillary inlet") +
+              ", FP64 oracle, one host thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(1, args.steps) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -302,6 +307,49 @@ def run_profile(args):
     return 0
 
 
+SWEEP = [(128, 16, 0, 4), (64, 16, 0, 4), (128, 4, 6, 4), (128, 8, 6, 4), (64, 4, 6, 4), (64, 4, 7, 4),
+         (64, 8, 7, 4), (32, 6, 8, 4), (32, 14, 8, 4), (128, 8, 2, 4), (128, 16, 2, 4), (128, 8, 1, 4),
+         (128, 4, 3, 4), (128, 16, 4, 4), (128, 16, 5, 4)]
+
+
+def run_sweep(args):
+    """Times every step-kernel variant over a few tilings on the workload
+    (CUDA events, L2 flushed as in the timed run); one JSON line each."""
+    import torch
+    from paper_0807_0602_gb300.build import build as build_lib
+    from paper_0807_0602_gb300.lbm import Lattice
+    build_lib()
+    c = workload()
+    g = c["geom"]
+    fluid_nodes = g["nx"] * g["ny"] - 2 * (g["cap_x1"] - g["cap_x0"])
+    peak, _ = peaks()
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    acc = torch.empty((), dtype=torch.float32, device="cuda")
+    for sched in SWEEP:
+        if args.precision == "f16s" and sched[2] == 1:
+            continue   # the cp.async kernel moves 4- or 8-byte elements only
+        with Lattice(dict(geom=g, params=c["params"], init=c["init"]), precision=args.precision, tile=sched[:2],
+                     kernel=sched[2:], graph_chunk=-1) as lat:
+            lat.step(20)
+            lat.sync()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                flush_w.zero_()
+                torch.sum(flush_r, 0, out=acc)
+                a.record()
+                lat.step(1)
+                b.record()
+            torch.cuda.synchronize()
+        us = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e3
+        gbs = fluid_nodes * BYTES_PER_NODE[args.precision] / (us * 1e-6) / 1e9
+        print(json.dumps({"schedule": list(sched), "kernel": KERNELS[sched[2]], "precision": args.precision,
+                          "us_per_step": us, "GLUPS": g["nx"] * g["ny"] / (us * 1e-6) / 1e9, "alg_GBs": gbs,
+                          "frac": gbs / peak, "steps": args.steps}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,11 +363,15 @@ def main():
                     help="only step the workload this many times (for ncu captures) and exit")
     ap.add_argument("--schedule", default="128,4,6,4",
                     help="tile_w,tile_h,kernel,depth used by --profile")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time every step-kernel variant on the workload (--steps steps each) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.sweep:
+        return run_sweep(args)
     args.warmup = max(3, args.warmup)
 
     world, rank, local = dist_setup(args.gpus)

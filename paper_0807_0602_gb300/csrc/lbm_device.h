@@ -30,14 +30,15 @@ struct RunDesc {
     double* log;              // device ring [cap][6] of this run, or nullptr
 };
 
-// A CTA's work: run, first collided column x0 (the CTA collides
-// min(W - 2, nx - x0) columns), rows [y0, y1).
 // column chunks (CTAs) per row of the mass reduction
 constexpr int kMassChunks = 4;
 
 // opt-in shared memory per CTA on sm_103a (227 KB)
 constexpr size_t kMaxSmemPerCta = 232448;
 
+// A CTA's work: run, first collided column x0 (the CTA collides
+// min(W - 2, nx - x0) columns, W - 8 for the TMA kernel, 2W - 4 for the pair
+// kernel), rows [y0, y1).
 struct Tile {
     int run, x0, y0, y1;
 };

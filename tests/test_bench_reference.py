@@ -1,0 +1,32 @@
+"""The bench's reference arm (the FP64 oracle on the host) keeps the JSON
+contract, including for runs too short to need a window of the workload,
+and only rank 0 prints."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(extra_env=None, *args):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                          capture_output=True, text=True, env=env, timeout=300)
+
+
+def test_reference_arm_short_run_prints_contract_line():
+    r = _run(None, "--steps", "2", "--warmup", "1")
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GLUPS" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert "8192x160" in line["config"]["sample"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run({"WORLD_SIZE": "2", "RANK": "1"}, "--steps", "2", "--warmup", "1")
+    assert r.returncode == 0 and r.stdout.strip() == ""
