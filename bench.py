@@ -350,6 +350,56 @@ def run_sweep(args):
     return 0
 
 
+def run_probe(args):
+    """The step's memory access pattern without its arithmetic (lbm_probe.h)
+    on the workload's grid and layout, at several resident-thread counts per
+    SM (set with unused dynamic shared memory), timed like the step (CUDA
+    events, L2 flushed before each pass); one JSON line per case."""
+    import ctypes
+    import torch
+    from paper_0807_0602_gb300 import _lib as L
+    from paper_0807_0602_gb300.build import build as build_lib
+    build_lib()
+    lib = L.load()
+    c = workload()
+    nx, ny = c["geom"]["nx"], c["geom"]["ny"]
+    pitch = (nx + 16 + 63) // 64 * 64
+    src = torch.rand(18 * ny * pitch, device="cuda")
+    dst = torch.zeros_like(src)
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    acc = torch.empty((), dtype=torch.float32, device="cuda")
+    peak, _ = peaks()
+    stream = torch.cuda.current_stream()
+    nodes = (nx - 2) * (ny - 2)
+    # 128-thread CTAs: resident threads per SM 2048 (no padding), 1024, 640, 512
+    occupancy = {2048: 0, 1024: 28 * 1024, 640: 45 * 1024, 512: 56 * 1024}
+    cases = [("pull", 0, 1), ("copy", 1, 1), ("march", 2, 4), ("march", 2, 8), ("march", 2, 16)]
+    for threads, smem in occupancy.items():
+        for name, pattern, rows in cases:
+            def launch():
+                rc = lib.lbm_probe_stream(pattern, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                          nx, ny, pitch, rows, 128, smem, ctypes.c_void_p(stream.cuda_stream))
+                if rc != 0:
+                    raise RuntimeError(f"lbm_probe_stream failed ({rc})")
+            for _ in range(3):
+                launch()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                flush_w.zero_()
+                torch.sum(flush_r, 0, out=acc)
+                a.record()
+                launch()
+                b.record()
+            torch.cuda.synchronize()
+            us = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e3
+            gbs = nodes * 144 / (us * 1e-6) / 1e9
+            print(json.dumps({"probe": name, "rows": rows, "threads_per_sm": threads, "us": us, "alg_GBs": gbs,
+                              "frac": gbs / peak, "grid": [nx, ny], "passes": args.steps}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,6 +415,8 @@ def main():
                     help="tile_w,tile_h,kernel,depth used by --profile")
     ap.add_argument("--sweep", action="store_true",
                     help="time every step-kernel variant on the workload (--steps steps each) and exit")
+    ap.add_argument("--probe", action="store_true",
+                    help="time the step's memory access pattern without arithmetic (--steps passes each) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -372,6 +424,8 @@ def main():
         return run_profile(args)
     if args.sweep:
         return run_sweep(args)
+    if args.probe:
+        return run_probe(args)
     args.warmup = max(3, args.warmup)
 
     world, rank, local = dist_setup(args.gpus)

@@ -1,0 +1,36 @@
+/* Streaming probes of the step's memory access pattern (diagnostic).
+ *
+ * The paper has no counterpart: these kernels reproduce only the memory
+ * traffic of one lattice step (18 population planes read and written per
+ * node, FP32) without its arithmetic, so that a measured step time can be
+ * set against what the access pattern itself reaches on the GPU.
+ *
+ * Layout: src and dst are device pointers to 18 planes of ny rows of `pitch`
+ * FP32 elements each (plane stride ny * pitch), x fastest; only interior
+ * nodes 1 <= x < nx - 1, 1 <= y < ny - 1 are touched, so no index wraps.
+ * The caller owns both buffers.
+ */
+#ifndef LBM_PROBE_H
+#define LBM_PROBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_PROBE_PULL 0  /* one thread per node: loads of F_i(x - c_i), store of every plane at x */
+#define LBM_PROBE_COPY 1  /* one thread per node: unshifted copy of the 18 planes */
+#define LBM_PROBE_MARCH 2 /* one thread per column marching `rows` rows, pull pattern per row */
+
+/* Launches one probe pass on `stream` (a cudaStream_t, NULL = default) with
+ * CTAs of `block` threads (a multiple of 32, at most 1024) and `smem_bytes`
+ * of dynamic shared memory that the kernel does not use: it only limits the
+ * CTAs resident per SM (0 .. 227 KB).  Returns 0 on success, 1 for invalid
+ * arguments (nothing launched), 3 if the launch failed. */
+int lbm_probe_stream(int pattern, const float* src, float* dst, int nx, int ny, int pitch, int rows, int block,
+                     int smem_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

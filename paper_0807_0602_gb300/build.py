@@ -27,6 +27,7 @@ UNITS = {
     "lbm_capi.cu": [],
     "mlp.cu": [],
     "lbm_noalloc.cu": [],
+    "stream_probe.cu": [],
 }
 
 

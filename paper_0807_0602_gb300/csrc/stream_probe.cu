@@ -1,0 +1,90 @@
+// Streaming probes (include/lbm_probe.h): the step kernel's memory access
+// pattern without its arithmetic, to measure what the pattern itself can
+// reach on this GPU.  Populations use the step's layout: 18 planes of
+// ny rows of `pitch` elements (FP32), interior nodes only (no wrap).
+#include <cuda_runtime.h>
+
+#include "lbm_probe.h"
+
+namespace {
+
+__constant__ int kDx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kDy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// one thread per node: the 18 pulled loads, then 18 stores
+__global__ void k_probe_pull(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny, int pitch,
+                             long long plane) {
+    extern __shared__ float occupancy_pad[];   // dynamic size only limits CTAs per SM
+    (void)occupancy_pad;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x + 1, y = blockIdx.y + 1;
+    if (x >= nx - 1 || y >= ny - 1) return;
+    float v[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        const int i = q % 9;
+        v[q] = __ldg(src + q * plane + (long long)(y - kDy[i]) * pitch + (x - kDx[i]));
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) dst[q * plane + (long long)y * pitch + x] = v[q];
+}
+
+// one thread per node, unshifted: a plain copy of 18 planes
+__global__ void k_probe_copy(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny, int pitch,
+                             long long plane) {
+    extern __shared__ float occupancy_pad[];
+    (void)occupancy_pad;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x + 1, y = blockIdx.y + 1;
+    if (x >= nx - 1 || y >= ny - 1) return;
+    float v[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) v[q] = __ldg(src + q * plane + (long long)y * pitch + x);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) dst[q * plane + (long long)y * pitch + x] = v[q];
+}
+
+// one thread per column, marching `rows` rows: the step kernels' march
+__global__ void k_probe_march(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny, int pitch,
+                              long long plane, int rows) {
+    extern __shared__ float occupancy_pad[];
+    (void)occupancy_pad;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x + 1, y0 = blockIdx.y * rows + 1;
+    if (x >= nx - 1) return;
+    for (int y = y0; y < y0 + rows && y < ny - 1; ++y) {
+        float v[18];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            const int i = q % 9;
+            v[q] = __ldg(src + q * plane + (long long)(y - kDy[i]) * pitch + (x - kDx[i]));
+        }
+#pragma unroll
+        for (int q = 0; q < 18; ++q) dst[q * plane + (long long)y * pitch + x] = v[q];
+    }
+}
+
+}  // namespace
+
+extern "C" int lbm_probe_stream(int pattern, const float* src, float* dst, int nx, int ny, int pitch, int rows,
+                                int block, int smem_bytes, void* stream) {
+    if (!src || !dst || nx < 3 || ny < 3 || pitch < nx || block < 32 || block > 1024 || block % 32 ||
+        smem_bytes < 0 || smem_bytes > 227 * 1024 || (pattern == LBM_PROBE_MARCH && rows < 1) ||
+        pattern < LBM_PROBE_PULL || pattern > LBM_PROBE_MARCH)
+        return 1;
+    const long long plane = (long long)ny * pitch;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    const void* fn = pattern == LBM_PROBE_PULL ? (const void*)k_probe_pull
+                     : pattern == LBM_PROBE_COPY ? (const void*)k_probe_copy
+                                                 : (const void*)k_probe_march;
+    if (smem_bytes > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return 3;
+    const dim3 blk(block);
+    if (pattern == LBM_PROBE_MARCH) {
+        const dim3 g((nx - 2 + block - 1) / block, (ny - 2 + rows - 1) / rows);
+        k_probe_march<<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch, plane, rows);
+    } else {
+        const dim3 g((nx - 2 + block - 1) / block, ny - 2);
+        if (pattern == LBM_PROBE_PULL) k_probe_pull<<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch, plane);
+        else k_probe_copy<<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch, plane);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}

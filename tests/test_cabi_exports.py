@@ -101,6 +101,17 @@ def test_invalid_arguments_are_rejected_without_touching_the_gpu(lib):
     assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
 
 
+def test_stream_probe_rejects_invalid_arguments_without_launching(lib):
+    null = ctypes.c_void_p(0)
+    buf = ctypes.c_void_p(256)   # never dereferenced: the checks come first
+    assert lib.lbm_probe_stream(0, null, buf, 64, 16, 64, 1, 128, 0, null) == 1
+    assert lib.lbm_probe_stream(3, buf, buf, 64, 16, 64, 1, 128, 0, null) == 1
+    assert lib.lbm_probe_stream(2, buf, buf, 64, 16, 64, 0, 128, 0, null) == 1
+    assert lib.lbm_probe_stream(0, buf, buf, 64, 16, 32, 1, 128, 0, null) == 1
+    assert lib.lbm_probe_stream(0, buf, buf, 64, 16, 64, 1, 100, 0, null) == 1
+    assert lib.lbm_probe_stream(0, buf, buf, 64, 16, 64, 1, 128, 300 * 1024, null) == 1
+
+
 def test_null_handles_and_status_strings(lib):
     from paper_0807_0602_gb300 import _lib as L
     assert lib.lbm_step(None, 1) == L.LBM_EINVAL
