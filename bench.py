@@ -223,6 +223,46 @@ def measure_batched(world: int, rank: int, stream, precision: str = "f32", steps
             "note": "inputs 24 GB >> L2, no flush needed; all nodes counted"}
 
 
+def measure_surrogate(reps: int = 50):
+    """The surrogate network's kernels (include/mlp.h): forward over 4096
+    rows, one Adam training step on 512 rows, and the proposal of couplings
+    for 64 target angles (1201 candidates each through one forward), timed
+    with CUDA events after warm-up; random weights, seeded inputs."""
+    import numpy as np
+    import torch
+    from paper_0807_0602_gb300.surrogate import Surrogate
+    rng = np.random.Generator(np.random.PCG64(5))
+    X = rng.uniform(-1, 1, size=(4096, 6))
+    T = rng.uniform(-1, 1, size=(4096, 3))
+    sur = Surrogate(X, T, seed=0, max_batch=4096)
+    xd = torch.as_tensor(sur.xn.fwd(X), dtype=torch.float32, device="cuda")
+    td = torch.as_tensor(sur.tn.fwd(T), dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    fwd_ms = timed(lambda: sur.net.forward(xd))
+    train_ms = timed(lambda: sur.net.train_step(xd[:512], td[:512], 1e-3))
+    targets = np.cos(np.radians(np.linspace(0.0, 90.0, 64)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sur.propose(targets, (1.0, 1.0, 1.0, 32.0))
+    prop_s = (time.perf_counter() - t0) / 5
+    flops_fwd = 2 * 4096 * (6 * 128 + 128 * 128 * 2 + 128 * 3)
+    return {"forward_rows_per_s": 4096 / (fwd_ms * 1e-3), "forward_ms_4096_rows": fwd_ms,
+            "forward_GFLOPs": flops_fwd / (fwd_ms * 1e-3) / 1e9, "train_step_ms_512_rows": train_ms,
+            "proposals_per_s": 64 / prop_s, "note": "bf16 mma.sync kernels; GEMMs of at most 128x128"}
+
+
 def cpu_baseline(budget_s: float = 15.0):
     """The FP64 oracle as it stands, single thread, on full 8192x160 steps."""
     import oracle
@@ -514,6 +554,7 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
 
     batched = None if args.no_batched else measure_batched(world, rank, stream, args.precision)
+    surrogate = measure_surrogate() if (rank == 0 and not args.no_batched) else None
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
@@ -529,6 +570,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [g["nx"], g["ny"]], "fluid_nodes": fluid_nodes,
+                   "fluid_GLUPS": value * fluid_nodes / nodes,
                    "precision": args.precision, "tile": list(sched[:2]),
                    "step_kernel": KERNELS[sched[2]], "log_every": log_every,
                    "l2": "flushed between timed steps: 256 MB written, then another 256 MB read",
@@ -541,6 +583,7 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched
+        line["surrogate"] = surrogate
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
