@@ -29,6 +29,17 @@ extern "C" {
 int lbm_probe_stream(int pattern, const float* src, float* dst, int nx, int ny, int pitch, int rows, int block,
                      int smem_bytes, void* stream);
 
+/* Failure-path self-test of the bounded waits (no counterpart in the paper).
+ * Launches one CTA that waits, with the same bounded mbarrier wait as the TMA
+ * step kernels, on a phase that nothing completes, giving up after `cycles`
+ * SM clock cycles (1e3 .. 4e9; the step kernels use 2e9, about 1 s), and
+ * reports what the step would: LBM_ETIMEOUT (5) when the wait ran out,
+ * LBM_OK if it completed, LBM_EINVAL for a cycle count out of range (nothing
+ * launched), LBM_ENOMEM / LBM_ECUDA on CUDA failures.  The kernel faults
+ * nothing and leaves the context usable; it synchronises `stream` (a
+ * cudaStream_t, NULL = default) and allocates and frees 4 bytes. */
+int lbm_selftest_wait_timeout(long long cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

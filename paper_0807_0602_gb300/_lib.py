@@ -53,6 +53,7 @@ class RunInfo(ctypes.Structure):
 
 # name -> (restype, argtypes); every function declared in include/lbm.h
 SIGNATURES = {
+    "lbm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong, c_void_p]),
     "lbm_probe_stream": (ctypes.c_int, [ctypes.c_int, c_void_p, c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, c_void_p]),
     "lbm_default_options": (None, [P(Options)]),

@@ -4,6 +4,8 @@
 // ny rows of `pitch` elements (FP32), interior nodes only (no wrap).
 #include <cuda_runtime.h>
 
+#include "lbm.h"
+#include "lbm_kernels.cuh"
 #include "lbm_probe.h"
 
 namespace {
@@ -87,4 +89,39 @@ extern "C" int lbm_probe_stream(int pattern, const float* src, float* dst, int n
         else k_probe_copy<<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch, plane);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+namespace {
+
+// One CTA waits, with the step kernels' bounded wait, on an mbarrier phase
+// that can never complete (an expected transaction that no copy delivers).
+__global__ void k_wait_selftest(long long limit, uint32_t* __restrict__ err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        sc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sc::mbar_expect_tx(&bar, 16u);   // the phase's only arrival; 16 bytes never come
+    if (!sc::mbar_wait(&bar, 0u, limit) && threadIdx.x == 0) atomicOr(err, sc::ERR_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" int lbm_selftest_wait_timeout(long long cycles, void* stream) {
+    if (cycles < 1000 || cycles > 4000000000LL) return LBM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* d_err = nullptr;
+    if (cudaMalloc(&d_err, sizeof(uint32_t)) != cudaSuccess) return LBM_ENOMEM;
+    uint32_t h_err = 0;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, s>>>(cycles, d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_err);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    return (h_err & sc::ERR_TIMEOUT) ? LBM_ETIMEOUT : LBM_OK;
 }

@@ -112,6 +112,12 @@ def test_stream_probe_rejects_invalid_arguments_without_launching(lib):
     assert lib.lbm_probe_stream(0, buf, buf, 64, 16, 64, 1, 128, 300 * 1024, null) == 1
 
 
+def test_wait_selftest_rejects_out_of_range_budgets_without_launching(lib):
+    from paper_0807_0602_gb300 import _lib as L
+    assert lib.lbm_selftest_wait_timeout(10, None) == L.LBM_EINVAL
+    assert lib.lbm_selftest_wait_timeout(5_000_000_000, None) == L.LBM_EINVAL
+
+
 def test_null_handles_and_status_strings(lib):
     from paper_0807_0602_gb300 import _lib as L
     assert lib.lbm_step(None, 1) == L.LBM_EINVAL
