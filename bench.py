@@ -223,6 +223,51 @@ def measure_batched(world: int, rank: int, stream, precision: str = "f32", steps
             "note": "inputs 24 GB >> L2, no flush needed; all nodes counted"}
 
 
+def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
+    """The error at which the throughput is quoted: FP32 and FP16-shifted
+    storage against the FP64 GPU build after `steps` steps of the workload,
+    and FP32 against FP64 on the first `batch_runs` runs of the uneven
+    ensemble.  Densities: max |n - n_64| over the max of |n_64| (per species,
+    worst of the two); fronts: max |z - z_64| in lattice units (bulk and both
+    precursors); mass: relative difference."""
+    import numpy as np
+    import workloads as W
+    from paper_0807_0602_gb300.lbm import Lattice
+
+    def state(runs, precision):
+        # one handle per run: a run that diverges makes its own handle's state sticky
+        from paper_0807_0602_gb300._lib import LbmError
+        out = []
+        for run in runs:
+            with Lattice(run, precision=precision) as lat:
+                lat.step(steps)
+                try:
+                    out.append((*lat.densities(), lat.interface(), lat.mass()))
+                except LbmError:
+                    nan = np.full((run["geom"]["ny"], run["geom"]["nx"]), np.nan)
+                    out.append((nan, nan, np.full(3, np.nan), np.full(2, np.nan)))
+        return out
+
+    def compare(ref, got):
+        # runs whose FP64 state stayed finite (the uneven ensemble samples parameters
+        # outside the scheme's stable band: some of its runs diverge)
+        ok = [i for i, r in enumerate(ref) if np.all(np.isfinite(r[0])) and np.all(np.isfinite(r[1]))]
+        pairs = [(ref[i], got[i]) for i in ok]
+        dn = max(float(np.max(np.abs(g[k] - r[k])) / max(float(np.max(np.abs(r[k]))), 1e-300))
+                 for r, g in pairs for k in (0, 1))
+        dz = max(float(np.nanmax(np.abs(np.asarray(g[2]) - np.asarray(r[2])))) for r, g in pairs)
+        dm = max(float(np.max(np.abs(g[3] - r[3]) / r[3])) for r, g in pairs)
+        return {"density_err_scale_rel": dn, "front_err_lu": dz, "mass_rel": dm, "finite_runs": len(ok)}
+
+    c = workload()
+    run = [dict(geom=c["geom"], params=c["params"], init=c["init"])]
+    ref = state(run, "f64")
+    res = {"steps": steps, "f32": compare(ref, state(run, "f32")), "f16s": compare(ref, state(run, "f16s"))}
+    runs = W.batch_uneven_capillaries(512, seed=3)[:batch_runs]
+    res["batched_f32"] = dict(compare(state(runs, "f64"), state(runs, "f32")), runs=batch_runs)
+    return res
+
+
 def measure_surrogate(reps: int = 50):
     """The surrogate network's kernels (include/mlp.h): forward over 4096
     rows, one Adam training step on 512 rows, and the proposal of couplings
@@ -555,6 +600,7 @@ def main():
 
     batched = None if args.no_batched else measure_batched(world, rank, stream, args.precision)
     surrogate = measure_surrogate() if (rank == 0 and not args.no_batched) else None
+    accuracy = measure_accuracy() if (rank == 0 and not args.no_batched) else None
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
@@ -584,6 +630,7 @@ def main():
     if not args.no_batched:
         line["batched"] = batched
         line["surrogate"] = surrogate
+        line["accuracy"] = accuracy
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
