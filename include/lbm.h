@@ -244,16 +244,29 @@ int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h);
  * kernel does not take that tiling.  Results do not depend on it. */
 int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 
-/* Full schedule of the step kernel: tiling plus the kernel variant
- * (LBM_KERNEL_REGISTER: pulled populations through registers;
- * LBM_KERNEL_ASYNC: through a depth-stage cp.async ring in shared memory,
- * depth 3 or 4, not available for LBM_F16S; LBM_KERNEL_TMA: source rows
- * streamed into a shared-memory ring by bulk copies (cp.async.bulk with
- * mbarrier completion), all precisions, every run needs nx >= 4; depth is
- * ignored; LBM_KERNEL_PIPELINED: register pull with the loads of the row
- * after next in flight during the collision, all precisions).  Results do
- * not depend on the schedule.  lbm_set_schedule
- * returns LBM_EINVAL for an unsupported combination. */
+/* Full schedule of the step kernel: tiling (tile_w, tile_h) plus the kernel
+ * variant and its depth.  Every variant computes the same bits for a given
+ * precision; they differ in how the pulled populations reach the collision:
+ *   LBM_KERNEL_REGISTER   through registers (tile_w in {64,128,256});
+ *   LBM_KERNEL_ASYNC      through a depth-stage cp.async ring in shared memory
+ *                         (depth 3 or 4; not for LBM_F16S);
+ *   LBM_KERNEL_TMA        through a ring of `depth` row slots (4, 6 or 8)
+ *                         filled by bulk copies with mbarrier completion;
+ *                         tile_w - 8 columns per CTA; the ring must fit in
+ *                         227 KB of shared memory; nx >= 4;
+ *   LBM_KERNEL_PIPELINED  parked in shared memory, with the loads of the row
+ *                         after next in flight during the collision (tile_w
+ *                         <= 128, FP64 <= 64);
+ *   LBM_KERNEL_SPLIT      one thread per species and node;
+ *   LBM_KERNEL_PREFETCH   through registers, rows prefetched into L2;
+ *   LBM_KERNEL_SMEM       parked in shared memory (the default; FP64 tile_w <= 128);
+ *   LBM_KERNEL_PAIR       two columns per thread (tile_w <= 128, FP64 64; nx >= 4);
+ *   LBM_KERNEL_TILE       one node per thread over tile_w x (tile_h + 2)
+ *                         threads (tile_w in {32, 64}, tile_h in {6, 14, 30},
+ *                         at most 1024 threads; nx >= 4).
+ * depth is read by LBM_KERNEL_ASYNC and LBM_KERNEL_TMA and must be 4 for the
+ * others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
+ * combination, leaving the schedule unchanged. */
 #define LBM_KERNEL_REGISTER 0
 #define LBM_KERNEL_ASYNC 1
 #define LBM_KERNEL_TMA 2

@@ -237,12 +237,14 @@ bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
     if (kvar == 8) {
         // one node per thread: W x (R + 2) threads, pulls read the ghost columns
         if (!((W == 32 && (R == 6 || R == 14 || R == 30)) || (W == 64 && (R == 6 || R == 14)))) return false;
+        if (depth != 4) return false;
         for (const RunDesc& rd : h->runs)
             if (rd.nx < 4) return false;
         return true;
     }
     if (W != 64 && W != 128 && W != 256) return false;
     if (kvar == 1 && (h->precision == LBM_F16S || (depth != 3 && depth != 4))) return false;
+    if (kvar != 1 && kvar != 2 && depth != 4) return false;   // depth is read by the ring kernels only
     // the shared-memory-staged kernel keeps 18 W populations per row parity in
     // static shared memory: FP64 at W = 256 would exceed the 48 KB static limit
     if (kvar == 6 && h->precision == LBM_F64 && W == 256) return false;

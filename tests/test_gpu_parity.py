@@ -339,3 +339,17 @@ def test_full_size_capillary_8192x160_first_steps_match_oracle():
             gA, gB = lat.densities()
         for g, r in ((gA, rA), (gB, rB)):
             assert np.max(np.abs(g - r)[fluid]) / np.max(np.abs(r)) <= 1e-5
+
+
+def test_schedule_validation_rejects_unsupported_combinations():
+    from paper_0807_0602_gb300 import _lib as L
+    geom, prm, kind = CASES["capillary64x18"]
+    nA, nB = _fields(geom, kind)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64") as lat:
+        before = lat.schedule
+        for bad in ((128, 4, 6, 3), (128, 4, 2, 5), (128, 4, 1, 6), (96, 4, 0, 4), (32, 4, 0, 4), (64, 7, 8, 4),
+                    (256, 4, 6, 4), (128, 4, 7, 4), (128, 4, 9, 4)):
+            with pytest.raises(L.LbmError) as e:
+                lat.schedule = bad
+            assert e.value.code == L.LBM_EINVAL
+            assert lat.schedule == before
