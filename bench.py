@@ -44,9 +44,9 @@ WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 p
             "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
 BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
 KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
-           "node-tile"]
+           "node-tile", "bidirectional"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
-                "k_step_smem", "k_step_pair", "k_step_tile"]
+                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir"]
 # committed ncu summaries of the step kernel on this workload, by kernel variant
 PROFILES = {6: os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt")}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
@@ -392,7 +392,8 @@ def run_profile(args):
     return 0
 
 
-SWEEP = [(128, 16, 0, 4), (64, 16, 0, 4), (128, 4, 6, 4), (128, 8, 6, 4), (64, 4, 6, 4), (64, 4, 7, 4),
+SWEEP = [(128, 16, 0, 4), (64, 16, 0, 4), (128, 4, 6, 4), (128, 8, 6, 4), (64, 4, 6, 4), (128, 8, 9, 4),
+         (128, 6, 9, 4), (128, 10, 9, 4), (64, 8, 9, 4), (64, 4, 7, 4),
          (64, 8, 7, 4), (32, 6, 8, 4), (32, 14, 8, 4), (128, 8, 2, 4), (128, 16, 2, 4), (128, 8, 1, 4),
          (128, 4, 3, 4), (128, 16, 4, 4), (128, 16, 5, 4)]
 

@@ -263,7 +263,10 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *   LBM_KERNEL_PAIR       two columns per thread (tile_w <= 128, FP64 64; nx >= 4);
  *   LBM_KERNEL_TILE       one node per thread over tile_w x (tile_h + 2)
  *                         threads (tile_w in {32, 64}, tile_h in {6, 14, 30},
- *                         at most 1024 threads; nx >= 4).
+ *                         at most 1024 threads; nx >= 4);
+ *   LBM_KERNEL_BIDIR      parked in shared memory, two groups of tile_w
+ *                         threads marching away from the tile's middle row
+ *                         (tile_w in {64, 128}, FP64 64).
  * depth is read by LBM_KERNEL_ASYNC and LBM_KERNEL_TMA and must be 4 for the
  * others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */
@@ -277,6 +280,7 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 #define LBM_KERNEL_PAIR 7        /* two columns per thread, vector loads and stores; nx >= 4 */
 #define LBM_KERNEL_TILE 8        /* one node per thread, W x (R + 2) tiles: W in {32, 64}, R in {6, 14, 30}
                                     (W = 64: R in {6, 14}); nx >= 4 */
+#define LBM_KERNEL_BIDIR 9       /* two thread groups marching away from the tile's middle row */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 

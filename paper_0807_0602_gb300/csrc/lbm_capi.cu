@@ -48,7 +48,8 @@ struct lbm_s {
                                    // loads of row r + 2 in flight, 4 species split over two threads per
                                    // node, 5 register pull with bulk L2 prefetch of rows ahead, 6 register
                                    // pull with the pulled rows parked in shared memory, 7 two columns per
-                                   // thread, 8 one node per thread over a W x (R + 2) tile
+                                   // thread, 8 one node per thread over a W x (R + 2) tile, 9 two thread
+                                   // groups marching away from the tile's middle row
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -226,6 +227,8 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
         return dispatch(h->precision, [&](auto L) { return L.step_smem(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 7)
         return dispatch(h->precision, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 9)
+        return dispatch(h->precision, [&](auto L) { return L.step_bidir(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 8)
         return dispatch(h->precision,
                         [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
@@ -233,7 +236,13 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
-    if (R < 1 || kvar < 0 || kvar > 8) return false;
+    if (R < 1 || kvar < 0 || kvar > 9) return false;
+    if (kvar == 9) {
+        // two groups of W threads, each staging 2 rows of 18 W populations
+        // statically: W in {64, 128} (FP64: 64)
+        if (depth != 4 || (W != 64 && W != 128) || (h->precision == LBM_F64 && W != 64)) return false;
+        return true;
+    }
     if (kvar == 8) {
         // one node per thread: W x (R + 2) threads, pulls read the ghost columns
         if (!((W == 32 && (R == 6 || R == 14 || R == 30)) || (W == 64 && (R == 6 || R == 14)))) return false;
@@ -362,7 +371,7 @@ int autotune(lbm_t* h, int64_t* n) {
     std::vector<Cand> cands;
     for (int W : {64, 128, 256})
         for (int R : Rs)
-            for (int kvar : {6, 0, 5, 3, 7, 2})
+            for (int kvar : {6, 9, 0, 5, 3, 7, 2})
                 if (schedule_ok(h, W, R, kvar, 4)) cands.push_back({W, R, kvar, 4});
     for (int W : {32, 64})
         for (int R : {6, 14})

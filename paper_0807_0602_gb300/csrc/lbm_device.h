@@ -80,6 +80,8 @@ struct Launch {
                                  cudaStream_t s);
     static cudaError_t step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s);
+    static cudaError_t step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
     static cudaError_t densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA,

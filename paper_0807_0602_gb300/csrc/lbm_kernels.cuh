@@ -831,6 +831,98 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
     }
 }
 
+// ---- bidirectional staged variant ---------------------------------------------
+// k_step_smem with two groups of W threads per CTA marching away from the
+// middle row m of the tile [y0, y1): group U pulls rows m - 1, m - 2, ... up
+// to the halo row y0 - 1 and collides m - 1 ... y0; group D pulls m, m + 1,
+// ... down to the halo row y1 and collides m ... y1 - 1.  The two groups
+// share their first rows through shared memory, so a tile of R rows pulls
+// R + 2 rows in R / 2 + 1 steps (k_step_smem: R + 2 steps).  Step k: pull,
+// barrier, collide; density slot of step k = group * 4 + (k & 3).
+template <typename S, int W>
+constexpr int kBidirMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 512 / W;   // 64 registers
+
+template <typename S, int W>
+__global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(const RunDesc* __restrict__ runs,
+                                                                              const Tile* __restrict__ tiles,
+                                                                              int parity) {
+    using C = typename Prec<S>::C;
+    __shared__ C sd[8][2][W];        // [group * 4 + step ring][species][column]
+    __shared__ C ps[2][2][18][W];    // [group][step parity][population][column]
+
+    const Tile tl = tiles[blockIdx.x];
+    const RunDesc& rd = runs[tl.run];
+    const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
+    const unsigned plane = (unsigned)rd.plane;
+    const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
+    const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
+    S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
+    StepCtx<S> cx;
+    cx.load(rd);
+    const int t = threadIdx.x % W, grp_d = threadIdx.x / W;   // grp_d 0: up (U), 1: down (D)
+    const StripCols sc(tl.x0, nx, W, t);
+    const int y0 = tl.y0, y1 = tl.y1;
+    const int m = y0 + (y1 - y0 + 1) / 2;                     // first row of D
+    const int nrows = grp_d == 0 ? m - y0 : y1 - m;          // rows this group collides
+    const int nsteps = (y1 - y0 + 1) / 2 + 1;                // same for both groups (U has the larger half)
+    // row pulled by this group at step k (the last one is the halo row)
+    auto row_at = [&](int k) { return grp_d == 0 ? m - 1 - k : m + k; };
+
+    auto pull = [&](int k, unsigned& smask) {
+        const int r = row_at(k);
+        const RowIdx q = rows_of(r, ny);
+        C nA = C(0), nB = C(0);
+        smask = 0;
+        if (sc.dcol) {
+            smask = nbr_solid(geo, sc.xm, sc.xc, sc.xp, q.rm, q.rw, q.rp);
+            if (!SOL(smask, 0, 0)) {
+                const unsigned bw = (unsigned)(q.rw * pitch), bm = (unsigned)(q.rm * pitch),
+                               bp = (unsigned)(q.rp * pitch);
+                C f[2][9];
+                pull_node<S>(src, plane, bw + sc.xc, bw + sc.xm, bw + sc.xp, bm + sc.xc, bp + sc.xc, bm + sc.xm,
+                             bm + sc.xp, bp + sc.xm, bp + sc.xp, smask, cx.sh, f);
+                nA = dens9(f[0]);
+                nB = dens9(f[1]);
+                if (sc.coll && k < nrows) {
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) ps[grp_d][k & 1][kk * 9 + i][t] = f[kk][i];
+                }
+            }
+        }
+        sd[grp_d * 4 + (k & 3)][0][t] = nA;
+        sd[grp_d * 4 + (k & 3)][1][t] = nB;
+    };
+
+    unsigned sm_prev = 0, sm_cur = 0;
+    for (int k = 0; k < nsteps; ++k) {
+        // this group pulls rows 0 .. nrows (the last is its halo row)
+        if (k <= nrows) pull(k, sm_cur);
+        __syncthreads();
+        // collide the row pulled at step k - 1: U row m - k, D row m + k - 1
+        if (k >= 1 && k <= nrows && sc.coll && !SOL(sm_prev, 0, 0)) {
+            const int r = grp_d == 0 ? m - k : m + k - 1;
+            const int own = grp_d * 4, other = (1 - grp_d) * 4;
+            // rows r - 1, r, r + 1 as density slots: the row beyond the middle at k = 1
+            // is the other group's step-0 row
+            const int s_new = own + (k & 3), s_row = own + ((k - 1) & 3);
+            const int s_old = k >= 2 ? own + ((k - 2) & 3) : other;
+            const int s_m = grp_d == 0 ? s_new : s_old, s_p = grp_d == 0 ? s_old : s_new;
+            C fc[2][9];
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fc[kk][i] = ps[grp_d][(k - 1) & 1][kk * 9 + i][t];
+            const int rw = rows_of(r, ny).rw;
+            collide_any<S, W, 0>(cx, fc, sm_prev, sd, s_m, s_row, s_p, t, dst, plane,
+                                 (unsigned)(rw * pitch + sc.xc), MomOut{nullptr, nullptr, 0}, 0, ghost_r(sc.xc, nx),
+                                 ghost_l(sc.xc, nx));
+        }
+        sm_prev = sm_cur;
+    }
+}
+
 // ---- two-columns-per-thread variant ---------------------------------------------
 // Thread t of a CTA of W threads owns the column pair (xa, xa + 1),
 // xa = x0 - 2 + 2t with x0 even, and marches down the rows of its tile like

@@ -194,6 +194,21 @@ cudaError_t Launch<S>::step_tile(int W, int R, const RunDesc* d_runs, const Tile
 }
 
 template <typename S>
+cudaError_t Launch<S>::step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: k_step_bidir<S, 64><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128:
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else k_step_bidir<S, 128><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
 cudaError_t Launch<S>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;

@@ -150,6 +150,10 @@ def test_results_independent_of_tiling_and_graphs(prec):
         scheds += [((128, 7), 5, (7, 4)), ((128, 37), 0, (7, 4))]
     scheds += [((32, 14), 0, (8, 4)), ((32, 6), -1, (8, 4)), ((64, 6), 5, (8, 4)), ((32, 30), 0, (8, 4)),
                ((64, 14), 7, (8, 4))]
+    scheds += [((64, 8), 0, (9, 4)), ((64, 1), -1, (9, 4)), ((64, 7), 5, (9, 4)), ((64, 37), 0, (9, 4)),
+               ((64, 2), 0, (9, 4))]
+    if prec != "f64":   # the bidirectional kernel takes W = 64 in FP64
+        scheds += [((128, 8), 0, (9, 4)), ((128, 5), 7, (9, 4))]
     outs = []
     for tile, chunk, kern in scheds:
         with Lattice(run, precision=prec, tile=tile, graph_chunk=chunk, rho_ref=(1.0, 1.0), kernel=kern) as lat:
@@ -163,13 +167,13 @@ def test_results_independent_of_tiling_and_graphs(prec):
 
 @pytest.mark.parametrize("name", ["capillary64x18", "odd17x9", "tiny5x4", "wide300x5", "box16x8"])
 @pytest.mark.parametrize("tile", [(64, 3), (128, 16), (256, 40)])
-@pytest.mark.parametrize("kernel", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("kernel", [2, 3, 4, 5, 6, 7, 8, 9])
 def test_tma_pipelined_split_kernels_fp64_match_oracle(name, tile, kernel):
     geom, prm, kind = CASES[name]
     nA, nB = _fields(geom, kind)
     if kernel == 8:   # the tile kernel's shapes: W x (R + 2) threads
         tile = {(64, 3): (32, 6), (128, 16): (32, 14), (256, 40): (64, 14)}[tile]
-    wmax = {3: 64, 6: 128, 7: 64}.get(kernel, 256)   # FP64 static shared memory bounds W
+    wmax = {3: 64, 6: 128, 7: 64, 9: 64}.get(kernel, 256)   # FP64 static shared memory bounds W
     if tile[0] > wmax:
         from paper_0807_0602_gb300 import _lib as L
         with pytest.raises(L.LbmError) as e:
@@ -348,7 +352,7 @@ def test_schedule_validation_rejects_unsupported_combinations():
     with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64") as lat:
         before = lat.schedule
         for bad in ((128, 4, 6, 3), (128, 4, 2, 5), (128, 4, 1, 6), (96, 4, 0, 4), (32, 4, 0, 4), (64, 7, 8, 4),
-                    (256, 4, 6, 4), (128, 4, 7, 4), (128, 4, 9, 4)):
+                    (256, 4, 6, 4), (128, 4, 7, 4), (128, 4, 9, 4), (64, 4, 9, 5), (128, 4, 10, 4)):
             with pytest.raises(L.LbmError) as e:
                 lat.schedule = bad
             assert e.value.code == L.LBM_EINVAL
