@@ -460,7 +460,8 @@ def run_probe(args):
     nodes = (nx - 2) * (ny - 2)
     # 128-thread CTAs: resident threads per SM 2048 (no padding), 1024, 640, 512
     occupancy = {2048: 0, 1024: 28 * 1024, 640: 45 * 1024, 512: 56 * 1024}
-    cases = [("pull", 0, 1), ("copy", 1, 1), ("march", 2, 4), ("march", 2, 8), ("march", 2, 16)]
+    cases = [("pull", 0, 1), ("copy", 1, 1), ("march", 2, 4), ("march", 2, 8), ("march", 2, 16),
+             ("pull-blocked", 3, 1), ("copy-blocked", 4, 1)]
     for threads, smem in occupancy.items():
         for name, pattern, rows in cases:
             def launch():
@@ -480,7 +481,8 @@ def run_probe(args):
                 b.record()
             torch.cuda.synchronize()
             us = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e3
-            gbs = nodes * 144 / (us * 1e-6) / 1e9
+            n_used = (nx - 64) * (ny - 2) if pattern >= 3 else nodes
+            gbs = n_used * 144 / (us * 1e-6) / 1e9
             print(json.dumps({"probe": name, "rows": rows, "threads_per_sm": threads, "us": us, "alg_GBs": gbs,
                               "frac": gbs / peak, "grid": [nx, ny], "passes": args.steps}), flush=True)
     return 0

@@ -20,6 +20,11 @@ extern "C" {
 #define LBM_PROBE_PULL 0  /* one thread per node: loads of F_i(x - c_i), store of every plane at x */
 #define LBM_PROBE_COPY 1  /* one thread per node: unshifted copy of the 18 planes */
 #define LBM_PROBE_MARCH 2 /* one thread per column marching `rows` rows, pull pattern per row */
+#define LBM_PROBE_PULL_BLOCKED 3 /* LBM_PROBE_PULL in a blocked layout: blocks of 32 columns holding all
+                                    18 planes contiguously, element (q, y, x) at
+                                    ((y (pitch / 32) + x / 32) 18 + q) 32 + x % 32; pitch a multiple of
+                                    32, nx >= 66, columns 32 .. nx - 33 */
+#define LBM_PROBE_COPY_BLOCKED 4 /* LBM_PROBE_COPY in the blocked layout */
 
 /* Launches one probe pass on `stream` (a cudaStream_t, NULL = default) with
  * CTAs of `block` threads (a multiple of 32, at most 1024) and `smem_bytes`

@@ -63,24 +63,56 @@ __global__ void k_probe_march(const float* __restrict__ src, float* __restrict__
     }
 }
 
+// Blocked layout: 32 columns of all 18 planes contiguous, element (q, y, x)
+// at ((y nb + x / 32) 18 + q) 32 + x % 32 with nb = pitch / 32 blocks per row.
+__device__ __forceinline__ long long blocked(int q, int y, int x, int nb) {
+    return ((long long)(y * nb + (x >> 5)) * 18 + q) * 32 + (x & 31);
+}
+
+// one thread per node (columns 32 .. nx - 33): pull or copy in the blocked layout
+template <bool PULL>
+__global__ void k_probe_blocked(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny, int nb) {
+    extern __shared__ float occupancy_pad[];
+    (void)occupancy_pad;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x + 32, y = blockIdx.y + 1;
+    if (x >= nx - 32 || y >= ny - 1) return;
+    float v[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        const int i = q % 9;
+        v[q] = PULL ? __ldg(src + blocked(q, y - kDy[i], x - kDx[i], nb)) : __ldg(src + blocked(q, y, x, nb));
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) dst[blocked(q, y, x, nb)] = v[q];
+}
+
 }  // namespace
 
 extern "C" int lbm_probe_stream(int pattern, const float* src, float* dst, int nx, int ny, int pitch, int rows,
                                 int block, int smem_bytes, void* stream) {
     if (!src || !dst || nx < 3 || ny < 3 || pitch < nx || block < 32 || block > 1024 || block % 32 ||
         smem_bytes < 0 || smem_bytes > 227 * 1024 || (pattern == LBM_PROBE_MARCH && rows < 1) ||
-        pattern < LBM_PROBE_PULL || pattern > LBM_PROBE_MARCH)
+        pattern < LBM_PROBE_PULL || pattern > LBM_PROBE_COPY_BLOCKED ||
+        (pattern >= LBM_PROBE_PULL_BLOCKED && (pitch % 32 || nx < 66)))
         return 1;
     const long long plane = (long long)ny * pitch;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    const void* fn = pattern == LBM_PROBE_PULL ? (const void*)k_probe_pull
-                     : pattern == LBM_PROBE_COPY ? (const void*)k_probe_copy
-                                                 : (const void*)k_probe_march;
+    const void* fn = pattern == LBM_PROBE_PULL          ? (const void*)k_probe_pull
+                     : pattern == LBM_PROBE_COPY        ? (const void*)k_probe_copy
+                     : pattern == LBM_PROBE_MARCH       ? (const void*)k_probe_march
+                     : pattern == LBM_PROBE_PULL_BLOCKED ? (const void*)k_probe_blocked<true>
+                                                         : (const void*)k_probe_blocked<false>;
     if (smem_bytes > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return 3;
     const dim3 blk(block);
-    if (pattern == LBM_PROBE_MARCH) {
+    if (pattern >= LBM_PROBE_PULL_BLOCKED) {
+        const dim3 g((nx - 64 + block - 1) / block, ny - 2);
+        if (pattern == LBM_PROBE_PULL_BLOCKED)
+            k_probe_blocked<true><<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch / 32);
+        else
+            k_probe_blocked<false><<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch / 32);
+    } else if (pattern == LBM_PROBE_MARCH) {
         const dim3 g((nx - 2 + block - 1) / block, (ny - 2 + rows - 1) / rows);
         k_probe_march<<<g, blk, smem_bytes, s>>>(src, dst, nx, ny, pitch, plane, rows);
     } else {
