@@ -47,8 +47,12 @@ KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "
            "node-tile", "bidirectional"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
                 "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir"]
-# committed ncu summaries of the step kernel on this workload, by kernel variant
-PROFILES = {6: os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt")}
+# committed ncu summaries of the step kernel on this workload, by (variant, tile)
+PROFILES = {
+    (6, (128, 4)): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
+    (6, (64, 4)): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 8)): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
+}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
                   for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "lbm_device.h")]
 
@@ -71,11 +75,12 @@ def read_traffic(kvar: int, tile):
     """DRAM bytes per step-kernel launch from the committed ncu summary of
     this kernel variant and tile, or None if there is none or the kernel
     sources changed since the counters were taken."""
-    if kvar not in PROFILES:
+    key = (int(kvar), (int(tile[0]), int(tile[1])))
+    if key not in PROFILES:
         return None
     try:
         kv = {}
-        with open(PROFILES[kvar]) as fh:
+        with open(PROFILES[key]) as fh:
             for line in fh:
                 if ":" in line:
                     k, v = line.split(":", 1)
