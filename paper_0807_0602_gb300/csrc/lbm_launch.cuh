@@ -2,9 +2,25 @@
 // by kernels_f64.cu and kernels_f32.cu.
 #pragma once
 
+#include <atomic>
+
 #include "lbm_kernels.cuh"
 
 namespace sc {
+
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` once per
+// device (one bit per device in `done`); two threads racing on a first launch
+// both set the same attribute, which is harmless.
+static inline cudaError_t ensure_dynamic_smem(const void* fn, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 static inline int clamp_grid(long long want, int cap) {
     if (want < 1) return 1;
@@ -36,13 +52,9 @@ cudaError_t Launch<S>::step(int W, const RunDesc* d_runs, const Tile* d_tiles, i
 template <typename S, int W, int D>
 static cudaError_t launch_async(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, cudaStream_t s) {
     constexpr size_t smem = async_smem_bytes<S, W, D>();
-    static bool configured = false;   // attribute set once per process and instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_async<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};   // per instantiation, one bit per device
+    const cudaError_t e = ensure_dynamic_smem((const void*)k_step_async<S, W, D>, (int)smem, configured);
+    if (e != cudaSuccess) return e;
     k_step_async<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity);
     return cudaGetLastError();
 }
@@ -74,13 +86,9 @@ static cudaError_t launch_tma(const RunDesc* d_runs, const Tile* d_tiles, int nt
     if constexpr (smem > kMaxSmemPerCta) {
         return cudaErrorInvalidValue;
     } else {
-        static bool configured = false;   // attribute set once per process and instantiation
-        if (!configured) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_step_tma<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
+        static std::atomic<unsigned long long> configured{0};   // per instantiation, one bit per device
+        const cudaError_t e = ensure_dynamic_smem((const void*)k_step_tma<S, W, D>, (int)smem, configured);
+        if (e != cudaSuccess) return e;
         k_step_tma<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
         return cudaGetLastError();
     }
