@@ -357,3 +357,56 @@ def test_schedule_validation_rejects_unsupported_combinations():
                 lat.schedule = bad
             assert e.value.code == L.LBM_EINVAL
             assert lat.schedule == before
+
+
+def _mask_case():
+    """A 40x24 periodic box with an explicit solid mask: blocks touching the
+    wrap columns 0 and nx - 1 and the wrap rows, a one-node obstacle, a thin
+    wall with a gap, and a fluid pocket enclosed on three sides."""
+    nx, ny = 40, 24
+    m = np.zeros((ny, nx), np.uint8)
+    m[0, :] = 1                       # bottom plate across the wrap
+    m[5:9, 0:3] = 1                   # block on the west edge
+    m[5:9, 37:40] = 1                 # its periodic neighbour on the east edge
+    m[12, 20] = 1                     # isolated solid node
+    m[15:23, 10] = 1                  # thin wall ...
+    m[18, 10] = 0                     # ... with a gap
+    m[14:20, 26] = 1                  # pocket: three sides
+    m[14, 26:31] = 1
+    m[19, 26:31] = 1
+    m[23, 33:40] = 1                  # top row next to the bottom plate (wraps)
+    geom = dict(nx=nx, ny=ny, cap_x0=0, cap_x1=0, y_bot=-1, y_top=-1, mask=m)
+    nA, nB = W.random_fields(geom, 7, 0.2, 1.2)
+    return geom, W.params(1.1, 1.0, 0.8, -0.2, 0.1), nA, nB
+
+
+MASK_SCHEDULES = [(None, None), ((128, 16), (0, 4)), ((64, 3), (1, 4)), ((64, 7), (2, 4)), ((64, 5), (3, 4)),
+                  ((128, 16), (4, 4)), ((128, 9), (5, 4)), ((64, 4), (6, 4)), ((64, 6), (7, 4)), ((32, 6), (8, 4)),
+                  ((64, 8), (9, 4))]
+
+
+def test_solid_mask_every_kernel_matches_oracle_fp64():
+    geom, prm, nA, nB = _mask_case()
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(30)
+    want = ref.populations()
+    for tile, kern in MASK_SCHEDULES:
+        kw = {} if kern is None else dict(tile=tile, kernel=kern)
+        with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", **kw) as lat:
+            lat.step(30)
+            got = lat.populations()
+            M = lat.mass()
+        assert np.array_equal(got, want), (tile, kern)
+        assert np.all(np.abs(M - ref.mass()) <= 1e-12 * ref.mass())
+
+
+def test_solid_mask_schedules_bit_identical_fp32():
+    geom, prm, nA, nB = _mask_case()
+    outs = []
+    for tile, kern in MASK_SCHEDULES:
+        kw = {} if kern is None else dict(tile=tile, kernel=kern)
+        with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f32", **kw) as lat:
+            lat.step(25)
+            outs.append(lat.populations())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
