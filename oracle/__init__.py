@@ -47,6 +47,7 @@ class _Params(ctypes.Structure):
         ("G", ctypes.c_double), ("Gw", ctypes.c_double * 2),
         ("tau", ctypes.c_double * 2), ("body", ctypes.c_double * 2),
         ("rho_bulk", ctypes.c_double),
+        ("alpha", ctypes.c_double * 2), ("mass", ctypes.c_double * 2),
     ]
 
 
@@ -77,6 +78,9 @@ def _load():
             lib.oc_interface.restype = ctypes.c_int
             lib.oc_interface.argtypes = [ctypes.c_void_p, dp]
             lib.oc_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            lib.oc_feq_alpha.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            lib.oc_pressure_general.restype = ctypes.c_double
+            lib.oc_pressure_general.argtypes = [ctypes.c_double] * 7
             lib.oc_pressure.restype = ctypes.c_double
             lib.oc_pressure.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             _lib = lib
@@ -87,16 +91,23 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def feq(n: float, ux: float, uy: float) -> np.ndarray:
-    """Eqs. 3-5 at alpha = 4/9 for one node: the 9 equilibrium populations."""
+def feq(n: float, ux: float, uy: float, alpha: float = 4.0 / 9.0) -> np.ndarray:
+    """Eqs. 3-5 for one node: the 9 equilibrium populations."""
     out = np.zeros(9)
-    _load().oc_feq(float(n), float(ux), float(uy), _dp(out))
+    _load().oc_feq_alpha(float(n), float(ux), float(uy), float(alpha), _dp(out))
     return out
 
 
-def pressure(nA, nB, G: float):
-    """Mixture pressure p = (n_A + n_B)/3 + G n_A n_B / 3 (Model section)."""
-    f = np.vectorize(lambda a, b: _load().oc_pressure(float(a), float(b), float(G)))
+def pressure(nA, nB, G: float, alpha=(4.0 / 9.0, 4.0 / 9.0), mass=(1.0, 1.0)):
+    """Mixture pressure p = m_A cA n_A + m_B cB n_B + G n_A n_B / 3 with
+    c^2 = 3 (1 - alpha) / 5 (Model section); (n_A + n_B)/3 + G n_A n_B / 3 at
+    alpha = 4/9, m = 1."""
+    lib = _load()
+    if tuple(alpha) == (4.0 / 9.0, 4.0 / 9.0) and tuple(mass) == (1.0, 1.0):
+        f = np.vectorize(lambda a, b: lib.oc_pressure(float(a), float(b), float(G)))
+    else:
+        f = np.vectorize(lambda a, b: lib.oc_pressure_general(float(a), float(b), float(G), float(alpha[0]),
+                                                              float(alpha[1]), float(mass[0]), float(mass[1])))
     return f(nA, nB)
 
 
@@ -105,7 +116,8 @@ class OracleLattice:
 
     ``geom`` keys: nx, ny, cap_x0, cap_x1, y_bot, y_top (-1 = none), optional
     ``mask`` (uint8 [ny, nx]).  ``params`` keys: G, G_Aw, G_Bw, tau_A, tau_B,
-    optional body (gx, gy) and rho_bulk.  ``nA0``/``nB0`` are the initial
+    optional body (gx, gy), rho_bulk, alpha (2-tuple, Eqs. 3-5, default 4/9)
+    and mass (2-tuple of molecular masses, default 1).  ``nA0``/``nB0`` are the initial
     densities ([ny, nx]); the state starts at rest in equilibrium.
     """
 
@@ -122,6 +134,10 @@ class OracleLattice:
         body = params.get("body", (0.0, 0.0))
         p.body[0], p.body[1] = float(body[0]), float(body[1])
         p.rho_bulk = float(params.get("rho_bulk", 2.0))
+        alpha = params.get("alpha", (4.0 / 9.0, 4.0 / 9.0))
+        mass = params.get("mass", (1.0, 1.0))
+        p.alpha[0], p.alpha[1] = float(alpha[0]), float(alpha[1])
+        p.mass[0], p.mass[1] = float(mass[0]), float(mass[1])
         self._p = p
         shape = (self.ny, self.nx)
         nA0 = np.ascontiguousarray(nA0, dtype=np.float64).reshape(shape)

@@ -22,8 +22,13 @@
  *
  * Readings taken where the paper is silent or ambiguous (all are part of the
  * canonical step this oracle defines):
- *   - alpha_k = 4/9 and m_k = 1, so Eqs. 3-5 reduce to the usual
- *     w_i n (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u), w = 4/9, 1/9, 1/36.
+ *   - Eqs. 3-5 are written as the usual w_i n (1 + 3 c.u + 9/2 (c.u)^2 -
+ *     3/2 u.u), w = 4/9, 1/9, 1/36, which they are at alpha_k = 4/9, plus
+ *     (A_i(alpha_k) - w_i) n with A_0 = alpha, A_1..4 = (1 - alpha)/5,
+ *     A_5..8 = (1 - alpha)/20 when alpha_k != 4/9 (only the isotropic part of
+ *     the equilibrium depends on alpha).  m_k weights the common velocity of
+ *     Eq. 8 (rho_k = m_k n_k, rho_k u_k = m_k j_k) and divides the velocity
+ *     shift of Eq. 7; defaults alpha_k = 4/9, m_k = 1.
  *   - The coupling is written with the w_i weights: G = 9 g, so the bulk
  *     acceleration is a_k = -G sum_i w_i n_kbar(x+c_i) c_i and F_k = n_k a_k.
  *     The wall force uses the same weights: a_k^w = -G_kw sum_i w_i s(x+c_i) c_i
@@ -41,10 +46,11 @@
  *   2. n_k = ((ft_0 + ft_1) + ...) + ft_8; j_k = sum_i ft_i c_i, i ascending
  *   3. S_kbar = sum_{i=1..8} (w_i n_kbar(x+c_i)) c_i, i ascending;
  *      Wl = sum_{i=1..8} (w_i s(x+c_i)) c_i; a_k = (-(G S_kbar) - (G_kw Wl)) + g
- *   4. U = (j_A/tau_A + j_B/tau_B) / (n_A/tau_A + n_B/tau_B),
- *      with 1/tau precomputed and multiplied
- *   5. u_k = U + tau_k a_k
- *   6. feq_i = (w_i n_k) (((1 + 3 cu) + 4.5 (cu cu)) - 1.5 usq)
+ *   4. U = (j_A mt_A + j_B mt_B) / (n_A mt_A + n_B mt_B), mt_k = m_k (1/tau_k)
+ *      precomputed (1/tau_k itself for m_k = 1)
+ *   5. u_k = U + tm_k a_k, tm_k = tau_k / m_k precomputed (tau_k for m_k = 1)
+ *   6. feq_i = (w_i n_k) (((1 + 3 cu) + 4.5 (cu cu)) - 1.5 usq), then
+ *      feq_i + (dA_i n_k) with dA_i = A_i(alpha_k) - w_i when alpha_k != 4/9
  *   7. F'_i = ft_i - (ft_i - feq_i) (1/tau_k)
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction).
@@ -77,6 +83,8 @@ typedef struct {
     double tau[2];           /* relaxation times */
     double body[2];          /* body acceleration (test-only drive) */
     double rho_bulk;         /* precursor threshold base: n_A < rho_bulk / 3 */
+    double alpha[2];         /* Eqs. 3-5 free parameter per species (4/9: standard D2Q9) */
+    double mass[2];          /* molecular masses m_k (rho_k = m_k n_k) */
 } oc_params;
 
 typedef struct {
@@ -113,14 +121,33 @@ static int is_solid(const oc_state* s, int x, int y) {
     return s->solid[(size_t)wrap(y, s->p.ny) * s->p.nx + wrap(x, s->p.nx)];
 }
 
-/* Eqs. 3-5 with alpha = 4/9 (canonical order, see header). */
-void oc_feq(double n, double ux, double uy, double* feq) {
+/* Isotropic part of Eqs. 3-5 minus its alpha = 4/9 value, dA_i = A_i(alpha) -
+ * w_i (A_0 = alpha, A_1..4 = (1 - alpha)/5, A_5..8 = (1 - alpha)/20); zero
+ * for alpha = 4/9. */
+static void alpha_shift(double alpha, double dA[3]) {
+    if (alpha == 4.0 / 9.0) {
+        dA[0] = dA[1] = dA[2] = 0.0;
+        return;
+    }
+    dA[0] = alpha - 4.0 / 9.0;
+    dA[1] = (1.0 - alpha) / 5.0 - 1.0 / 9.0;
+    dA[2] = (1.0 - alpha) / 20.0 - 1.0 / 36.0;
+}
+
+/* Eqs. 3-5 for free alpha (canonical order, see header). */
+void oc_feq_alpha(double n, double ux, double uy, double alpha, double* feq) {
+    double dA[3];
+    alpha_shift(alpha, dA);
     double usq = ux * ux + uy * uy;
     for (int i = 0; i < 9; ++i) {
         double cu = CX[i] * ux + CY[i] * uy;
         feq[i] = (weight(i) * n) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * usq);
+        if (alpha != 4.0 / 9.0) feq[i] = feq[i] + dA[i == 0 ? 0 : (i <= 4 ? 1 : 2)] * n;
     }
 }
+
+/* Eqs. 3-5 with alpha = 4/9. */
+void oc_feq(double n, double ux, double uy, double* feq) { oc_feq_alpha(n, ux, uy, 4.0 / 9.0, feq); }
 
 /* Left-hand side of Eq. 2 with half-way bounce-back at solid nodes:
  * the population moving along c_i arrives at x from x - c_i. */
@@ -175,7 +202,7 @@ static void accel_at(const oc_state* s, const double* n, int x, int y, double a[
     }
 }
 
-/* Momentum j_k = sum_i c_i f_i (m_k = 1), i ascending. */
+/* Number-density momentum j_k = sum_i c_i f_i, i ascending (rho_k u_k = m_k j_k). */
 static void momentum_at(const oc_state* s, const double* f, int k, int x, int y, double j[2]) {
     const oc_params* p = &s->p;
     double jx = 0.0, jy = 0.0;
@@ -192,6 +219,8 @@ static void momentum_at(const oc_state* s, const double* f, int k, int x, int y,
 static void collide(oc_state* s, const double* ft, const double* n, double* Fout) {
     const oc_params* p = &s->p;
     double itau[2] = {1.0 / p->tau[0], 1.0 / p->tau[1]};
+    double mt[2] = {p->mass[0] * itau[0], p->mass[1] * itau[1]};
+    double tm[2] = {p->tau[0] / p->mass[0], p->tau[1] / p->mass[1]};
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             if (is_solid(s, x, y)) {
@@ -206,13 +235,13 @@ static void collide(oc_state* s, const double* ft, const double* n, double* Fout
             }
             accel_at(s, n, x, y, a);
             double U[2];
-            double den = nk[0] * itau[0] + nk[1] * itau[1];
-            for (int d = 0; d < 2; ++d) U[d] = (j[0][d] * itau[0] + j[1][d] * itau[1]) / den;
+            double den = nk[0] * mt[0] + nk[1] * mt[1];
+            for (int d = 0; d < 2; ++d) U[d] = (j[0][d] * mt[0] + j[1][d] * mt[1]) / den;
             for (int k = 0; k < 2; ++k) {
                 double ueq[2];
-                for (int d = 0; d < 2; ++d) ueq[d] = U[d] + p->tau[k] * a[k][d];
+                for (int d = 0; d < 2; ++d) ueq[d] = U[d] + tm[k] * a[k][d];
                 double feq[9];
-                oc_feq(nk[k], ueq[0], ueq[1], feq);
+                oc_feq_alpha(nk[k], ueq[0], ueq[1], p->alpha[k], feq);
                 for (int i = 0; i < 9; ++i) {
                     double f = ft[IDX(p, k, i, x, y)];
                     Fout[IDX(p, k, i, x, y)] = f - (f - feq[i]) * itau[k];
@@ -226,6 +255,8 @@ static void collide(oc_state* s, const double* ft, const double* n, double* Fout
 oc_state* oc_create(const oc_params* prm, const uint8_t* mask, const double* nA0, const double* nB0) {
     if (!prm || prm->nx < 1 || prm->ny < 1 || !nA0 || !nB0) return NULL;
     if (!(prm->tau[0] > 0.5) || !(prm->tau[1] > 0.5)) return NULL;
+    if (!(prm->mass[0] > 0.0) || !(prm->mass[1] > 0.0)) return NULL;
+    if (!(prm->alpha[0] < 1.0) || !(prm->alpha[1] < 1.0)) return NULL;
     oc_state* s = (oc_state*)calloc(1, sizeof(oc_state));
     s->p = *prm;
     size_t N = NODES(prm);
@@ -242,7 +273,7 @@ oc_state* oc_create(const oc_params* prm, const uint8_t* mask, const double* nA0
             for (int k = 0; k < 2; ++k) {
                 double n0 = (k == 0 ? nA0 : nB0)[(size_t)y * prm->nx + x];
                 double feq[9];
-                oc_feq(n0, 0.0, 0.0, feq);
+                oc_feq_alpha(n0, 0.0, 0.0, prm->alpha[k], feq);
                 for (int i = 0; i < 9; ++i) s->F[IDX(prm, k, i, x, y)] = feq[i];
             }
         }
@@ -320,8 +351,9 @@ void oc_accel(const oc_state* s, const double* nA, const double* nB, double* out
 }
 
 /* Whole-fluid velocity at the current time (Model section, below Eq. 12):
- * rho u = sum_k rho_k u_k + (1/2) sum_k F_k, computed from the streamed
- * populations of the last step.  Returns 0 at t = 0 (the fluid is at rest). */
+ * rho u = sum_k rho_k u_k + (1/2) sum_k F_k with rho = sum_k m_k n_k and
+ * rho_k u_k = m_k j_k, computed from the streamed populations of the last
+ * step.  Returns 0 at t = 0 (the fluid is at rest). */
 int oc_velocity(const oc_state* s, double* ux, double* uy) {
     const oc_params* p = &s->p;
     size_t N = NODES(p);
@@ -343,8 +375,10 @@ int oc_velocity(const oc_state* s, double* ux, double* uy) {
             momentum_at(s, ft, 1, x, y, jB);
             accel_at(s, n, x, y, a);
             double nA = n[q], nB = n[N + q];
-            ux[q] = ((jA[0] + jB[0]) + 0.5 * ((nA * a[0][0]) + (nB * a[1][0]))) / (nA + nB);
-            uy[q] = ((jA[1] + jB[1]) + 0.5 * ((nA * a[0][1]) + (nB * a[1][1]))) / (nA + nB);
+            const double mA = p->mass[0], mB = p->mass[1];
+            const double rho = (mA * nA) + (mB * nB);
+            ux[q] = (((mA * jA[0]) + (mB * jB[0])) + 0.5 * ((nA * a[0][0]) + (nB * a[1][0]))) / rho;
+            uy[q] = (((mA * jA[1]) + (mB * jB[1])) + 0.5 * ((nA * a[0][1]) + (nB * a[1][1]))) / rho;
         }
     free(ft);
     free(n);
@@ -365,7 +399,7 @@ void oc_mass(const oc_state* s, double* M) {
     }
 }
 
-/* Total post-collision momentum sum_x sum_k sum_i c_i F_i. */
+/* Total post-collision momentum sum_x sum_k m_k sum_i c_i F_i (rho_k u_k = m_k j_k). */
 void oc_momentum(const oc_state* s, double* P) {
     const oc_params* p = &s->p;
     double px = 0.0, py = 0.0;
@@ -375,8 +409,8 @@ void oc_momentum(const oc_state* s, double* P) {
                 if (is_solid(s, x, y)) continue;
                 double j[2];
                 momentum_at(s, s->F, k, x, y, j);
-                px = px + j[0];
-                py = py + j[1];
+                px = px + p->mass[k] * j[0];
+                py = py + p->mass[k] * j[1];
             }
     P[0] = px;
     P[1] = py;
@@ -444,4 +478,12 @@ int oc_interface(const oc_state* s, double* out) {
  * G n_A n_B / 3. */
 double oc_pressure(double nA, double nB, double G) {
     return (nA + nB) / 3.0 + G * nA * nB / 3.0;
+}
+
+/* The same for free alpha_k and m_k: the momentum flux of species k carries
+ * m_k n_k (c_s^k)^2 with (c_s^k)^2 = 3 (1 - alpha_k) / 5 (Model section):
+ * p = m_A cA n_A + m_B cB n_B + G n_A n_B / 3. */
+double oc_pressure_general(double nA, double nB, double G, double alphaA, double alphaB, double mA, double mB) {
+    double cA = 3.0 * (1.0 - alphaA) / 5.0, cB = 3.0 * (1.0 - alphaB) / 5.0;
+    return (mA * cA * nA + mB * cB * nB) + G * nA * nB / 3.0;
 }

@@ -442,3 +442,63 @@ def test_capillary_front_follows_eq16_with_laplace_gamma_and_droplet_angle():
     assert r2_16 > 0.999 and r2_16 > r2_w
     ratio = A16 / (gamma * H * math.cos(math.radians(theta)) / (6.0 * mu * L))
     assert 0.55 < ratio < 1.2
+
+
+# ---- free alpha_k and molecular masses m_k (Model section, Eqs. 3-8) -------------
+
+@pytest.mark.parametrize("alpha", [0.2, 4.0 / 9.0, 0.8])
+def test_equilibrium_moments_for_free_alpha(alpha):
+    """Eqs. 3-5 at any alpha: zeroth and first moments n and n u, second
+    moment n (u u + c_s^2 I) with c_s^2 = 3 (1 - alpha) / 5 (the sound speed
+    the paper attaches to alpha), and at rest the isotropic values the paper
+    prints: alpha n, (1 - alpha) n / 5, (1 - alpha) n / 20."""
+    c = _eq6_velocities()
+    n, u = 1.3, (0.05, -0.03)
+    f = oracle.feq(n, *u, alpha=alpha)
+    cs2 = 3.0 * (1.0 - alpha) / 5.0
+    assert abs(f.sum() - n) < 1e-14
+    for d in range(2):
+        assert abs(sum(f[i] * c[i][d] for i in range(9)) - n * u[d]) < 1e-14
+        for e in range(2):
+            m2 = sum(f[i] * c[i][d] * c[i][e] for i in range(9))
+            assert abs(m2 - n * (u[d] * u[e] + (cs2 if d == e else 0.0))) < 1e-14
+    rest = oracle.feq(n, 0.0, 0.0, alpha=alpha)
+    assert np.allclose(rest, [alpha * n] + [(1 - alpha) * n / 5] * 4 + [(1 - alpha) * n / 20] * 4, rtol=0, atol=1e-15)
+
+
+def test_mass_weighted_momentum_is_conserved_with_unequal_masses():
+    """Eq. 8's U makes the collision conserve sum_k rho_k u_k = sum_k m_k j_k,
+    and the pair force of Eq. 9 sums to zero, so the mass-weighted momentum of
+    a periodic box is conserved for any m_k, tau_k, alpha_k; the unweighted
+    number momentum is not (a dropped m_k in Eq. 7 or 8 fails this)."""
+    geom = W.periodic_box(20, 14)
+    prm = dict(W.params(1.0, 0.8, 1.3), alpha=(4.0 / 9.0, 0.7), mass=(1.0, 2.5))
+    o = _lattice(geom, prm, W.random_fields(geom, 3, 0.2, 1.2))
+    P0 = o.momentum()
+    F = o.populations()
+    j0 = np.array([sum(F[k, i] * _eq6_velocities()[i][0] for i in range(9)).sum() for k in range(2)])
+    o.step(60)
+    P1 = o.momentum()
+    F = o.populations()
+    j1 = np.array([sum(F[k, i] * _eq6_velocities()[i][0] for i in range(9)).sum() for k in range(2)])
+    scale = np.abs(F).sum()
+    assert np.all(np.abs(P1 - P0) <= 1e-12 * scale)
+    assert abs((j1.sum() - j0.sum())) > 1e-6 * scale       # number momentum alone moves
+
+
+def test_flat_interface_pressure_balance_with_free_alpha_and_mass():
+    """A steady flat interface between a species with alpha = 4/9 and one with
+    alpha = 0.8 and twice the molecular mass: the momentum flux of species k
+    carries m_k n_k c_s^2(alpha_k), so p = m_A cA n_A + m_B cB n_B + G n_A n_B/3
+    is equal in both bulks; the alpha = 4/9, m = 1 formula is not."""
+    geom = W.periodic_box(64, 1)
+    G, alpha, mass = 1.4, (4.0 / 9.0, 0.8), (1.0, 2.0)
+    o = _lattice(geom, dict(W.params(G, 1.0, 1.3), alpha=alpha, mass=mass), W.slab_fields(geom, 16, 40))
+    _relax(o, 20000, 2000)
+    a, b = o.densities()
+    assert a[0, 28] > 1.5 and b[0, 52] > 1.5          # separated
+    pA = oracle.pressure(a[0, 28], b[0, 28], G, alpha, mass)
+    pB = oracle.pressure(a[0, 52], b[0, 52], G, alpha, mass)
+    assert abs(pA - pB) <= 1e-8 * pA
+    qA, qB = oracle.pressure(a[0, 28], b[0, 28], G), oracle.pressure(a[0, 52], b[0, 52], G)
+    assert abs(qA - qB) > 0.1 * qA
