@@ -57,9 +57,15 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
                   for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "lbm_device.h")]
 
 
+# (alpha_A, alpha_B, m_A, m_B) of --species, or None for alpha = 4/9, m = 1
+SPECIES = None
+
+
 def workload(tau_B: float = 1.0):
     import workloads as W
     c = W.config_capillary_8192x160(tau_B=tau_B)
+    if SPECIES is not None:
+        c["params"] = dict(c["params"], alpha=tuple(SPECIES[:2]), mass=tuple(SPECIES[2:]))
     return c
 
 
@@ -76,7 +82,7 @@ def read_traffic(kvar: int, tile):
     this kernel variant and tile, or None if there is none or the kernel
     sources changed since the counters were taken."""
     key = (int(kvar), (int(tile[0]), int(tile[1])))
-    if key not in PROFILES:
+    if key not in PROFILES or SPECIES is not None:   # the summaries cover the alpha = 4/9, m = 1 kernels
         return None
     try:
         kv = {}
@@ -508,9 +514,16 @@ def main():
                     help="tile_w,tile_h,kernel,depth used by --profile")
     ap.add_argument("--sweep", action="store_true",
                     help="time every step-kernel variant on the workload (--steps steps each) and exit")
+    ap.add_argument("--species", default=None,
+                    help="alpha_A,alpha_B,m_A,m_B: rest fractions (Eqs. 3-5) and molecular masses of the species")
     ap.add_argument("--probe", action="store_true",
                     help="time the step's memory access pattern without arithmetic (--steps passes each) and exit")
     args = ap.parse_args()
+    if args.species:
+        global SPECIES
+        SPECIES = tuple(float(v) for v in args.species.split(","))
+        if len(SPECIES) != 4:
+            ap.error("--species takes alpha_A,alpha_B,m_A,m_B")
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
@@ -629,7 +642,9 @@ def main():
                    "step_kernel": KERNELS[sched[2]], "log_every": log_every,
                    "l2": "flushed between timed steps: 256 MB written, then another 256 MB read",
                    "state_finite": finite,
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "species": ({"alpha": list(SPECIES[:2]), "mass": list(SPECIES[2:])} if SPECIES
+                               else {"alpha": [4 / 9, 4 / 9], "mass": [1.0, 1.0]})},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": gpu_launches,

@@ -121,7 +121,20 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  * body          constant body acceleration added to both species' a_k
  *               (drives the Poiseuille check; 0 for capillary filling).
  * alloc/free    optional device allocator; NULL = cudaMallocAsync on stream.
- * stream        cudaStream_t of all work; NULL = legacy default stream. */
+ * stream        cudaStream_t of all work; NULL = legacy default stream.
+ * alpha         rest fraction alpha_k of each species' equilibrium (Model
+ *               section, Eqs. 3-5): f_0^eq carries alpha n, the axis and
+ *               diagonal directions (1 - alpha)/5 and (1 - alpha)/20 of n,
+ *               sound speed c_s^2 = 3 (1 - alpha)/5.  0 <= alpha < 1;
+ *               default 4/9 (the standard D2Q9 weights, c_s^2 = 1/3).
+ * molecular_mass  m_k > 0 of each species (rho_k = m_k n_k, Model section):
+ *               enters the common velocity of Eq. 8 as the weights m_k/tau_k,
+ *               the shift of Eq. 7 as tau_k/m_k, and the whole-fluid
+ *               velocity of lbm_velocity as sum m_k j_k over sum m_k n_k.
+ *               Default 1.  alpha = 4/9 and m = 1 give the same bits as a
+ *               handle built without these fields.
+ * A zeroed structure is not valid (molecular_mass = 0): start from
+ * lbm_default_options. */
 typedef struct lbm_options {
     int32_t precision;
     int32_t log_every;
@@ -138,6 +151,8 @@ typedef struct lbm_options {
     lbm_free_fn free;
     void* alloc_ctx;
     void* stream;
+    double alpha[2];
+    double molecular_mass[2];
 } lbm_options;
 
 /* Description of one run's device storage (for callers that read the raw
@@ -204,8 +219,9 @@ int lbm_run_info_get(const lbm_t* h, int run, lbm_run_info* info);
 int lbm_densities(lbm_t* h, int run, double* nA, double* nB, int on_device);
 
 /* Whole-fluid velocity at time t >= 1 (Model section, below Eq. 12):
- * rho u = sum_k rho_k u_k + (1/2) sum_k F_k with the streamed populations
- * and the forces of the last step.  ux, uy: [ny][nx] FP64, solid nodes 0.
+ * rho u = sum_k m_k j_k + (1/2) sum_k F_k, rho = sum_k m_k n_k, with the
+ * streamed populations and the forces of the last step.  ux, uy: [ny][nx]
+ * FP64, solid nodes 0.
  * At t = 0 the fluid is at rest and zeros are written.  on_device as above. */
 int lbm_velocity(lbm_t* h, int run, double* ux, double* uy, int on_device);
 
@@ -287,7 +303,8 @@ int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 /* Writes a checkpoint (header, parameters, populations of time t, log) to
  * path; lbm_load re-creates the handle so that stepping on gives results
  * bit-identical to an uninterrupted run.  Both synchronise.  LBM_EIO on
- * file errors. */
+ * file errors.  The file keeps alpha and molecular_mass (format version 2);
+ * version 1 files load with the defaults 4/9 and 1. */
 int lbm_save(lbm_t* h, const char* path);
 int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
 

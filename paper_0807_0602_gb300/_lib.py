@@ -41,6 +41,7 @@ class Options(ctypes.Structure):
         ("tile_w", c_int32), ("tile_h", c_int32), ("graph_chunk", c_int32), ("reserved0", c_int32),
         ("rho_ref", c_double * 2), ("rho_bulk", c_double), ("body", c_double * 2),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", c_void_p), ("stream", c_void_p),
+        ("alpha", c_double * 2), ("molecular_mass", c_double * 2),
     ]
 
 

@@ -23,7 +23,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 UNITS = {
     "kernels_f64.cu": ["--fmad=false"],
+    "kernels_gen_f64.cu": ["--fmad=false"],
     "kernels_f32.cu": [],
+    "kernels_gen_f32.cu": [],
+    "kernels_f16.cu": [],
+    "kernels_gen_f16.cu": [],
     "lbm_capi.cu": [],
     "mlp.cu": [],
     "lbm_noalloc.cu": [],

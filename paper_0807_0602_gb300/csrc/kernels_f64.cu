@@ -1,4 +1,4 @@
-// FP64 instantiation of the step and its reductions.  Built with
+// FP64 instantiation of the step (standard species) and its reductions.  Built with
 // --fmad=false: every product and sum of the canonical order is rounded on
 // its own, so the results equal a plain FP64 evaluation of the same order.
 #include "lbm_launch.cuh"
@@ -35,5 +35,6 @@ cudaError_t launch_log_advance(LogCtl lc, cudaStream_t s) {
 }
 
 template struct Launch<double>;
+template struct Step<double, false>;
 
 }  // namespace sc

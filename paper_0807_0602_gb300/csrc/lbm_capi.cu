@@ -43,6 +43,7 @@ struct lbm_s {
     size_t d_tiles_cap = 0;
     std::vector<int> tile_begin, tile_count;
     int tile_w = 128, tile_h = 4;
+    bool gen = false;              // some alpha_k != 4/9 or m_k != 1 (RunDesc::gen)
     int kvar = 6, depth = 4;       // step kernel (LBM_KERNEL_* of lbm.h): 0 register pull, 1 cp.async
                                    // stages of depth D, 2 TMA ring of D row slots, 3 staged pull with the
                                    // loads of row r + 2 in flight, 4 species split over two threads per
@@ -122,6 +123,17 @@ cudaError_t dispatch(int precision, F&& f) {
     }
 }
 
+// Step launchers of the handle's precision and species model (gen: some
+// alpha_k != 4/9 or m_k != 1).
+template <typename F>
+cudaError_t dispatch_step(const lbm_t* h, F&& f) {
+    switch (h->precision) {
+        case LBM_F64: return h->gen ? f(sc::Step<double, true>()) : f(sc::Step<double, false>());
+        case LBM_F32: return h->gen ? f(sc::Step<float, true>()) : f(sc::Step<float, false>());
+        default: return h->gen ? f(sc::Step<__half, true>()) : f(sc::Step<__half, false>());
+    }
+}
+
 bool finite(double v) { return std::isfinite(v); }
 
 int round_pitch(int nx);
@@ -150,6 +162,11 @@ int validate_options(const lbm_options& o) {
         !finite(o.body[1]))
         return LBM_EINVAL;
     if ((o.alloc == nullptr) != (o.free == nullptr)) return LBM_EINVAL;
+    for (int k = 0; k < 2; ++k) {
+        // Eqs. 3-5 need 0 <= alpha < 1 (positive moving weights); rho_k = m_k n_k needs m_k > 0
+        if (!finite(o.alpha[k]) || !(o.alpha[k] >= 0.0) || !(o.alpha[k] < 1.0)) return LBM_EINVAL;
+        if (!finite(o.molecular_mass[k]) || !(o.molecular_mass[k] > 0.0)) return LBM_EINVAL;
+    }
     return LBM_OK;
 }
 
@@ -212,27 +229,28 @@ sc::LogCtl logctl(lbm_t* h) {
 cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     const int W = h->tile_w, nt = (int)h->tiles.size();
     if (h->kvar == 1)
-        return dispatch(h->precision,
-                        [&](auto L) { return L.step_async(W, h->depth, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h,
+                             [&](auto L) { return L.step_async(W, h->depth, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 2)
-        return dispatch(h->precision,
-                        [&](auto L) { return L.step_tma(W, h->depth, h->d_runs, h->d_tiles, nt, parity, h->d_err, s); });
+        return dispatch_step(h, [&](auto L) {
+            return L.step_tma(W, h->depth, h->d_runs, h->d_tiles, nt, parity, h->d_err, s);
+        });
     if (h->kvar == 3)
-        return dispatch(h->precision, [&](auto L) { return L.step_pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 4)
-        return dispatch(h->precision, [&](auto L) { return L.step_split(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_split(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 5)
-        return dispatch(h->precision, [&](auto L) { return L.step_l2pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_l2pf(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 6)
-        return dispatch(h->precision, [&](auto L) { return L.step_smem(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_smem(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 7)
-        return dispatch(h->precision, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 9)
-        return dispatch(h->precision, [&](auto L) { return L.step_bidir(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 8)
-        return dispatch(h->precision,
-                        [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
-    return dispatch(h->precision, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h,
+                             [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
+    return dispatch_step(h, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
@@ -511,11 +529,30 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
         rd.tauB = tau_B[r];
         rd.itauA = 1.0 / tau_A[r];
         rd.itauB = 1.0 / tau_B[r];
+        rd.mA = opt.molecular_mass[0];
+        rd.mB = opt.molecular_mass[1];
+        rd.mitauA = rd.mA * rd.itauA;
+        rd.mitauB = rd.mB * rd.itauB;
+        rd.taumA = tau_A[r] / rd.mA;
+        rd.taumB = tau_B[r] / rd.mB;
+        rd.gen = rd.mA != 1.0 || rd.mB != 1.0;
+        for (int k = 0; k < 2; ++k) {
+            // A_i(alpha) - w_i of Eqs. 3-5: rest alpha - 4/9, axis (1 - alpha)/5 - 1/9,
+            // diagonal (1 - alpha)/20 - 1/36
+            const double a = opt.alpha[k];
+            const bool dflt = a == 4.0 / 9.0;
+            rd.dA[k][0] = dflt ? 0.0 : a - 4.0 / 9.0;
+            rd.dA[k][1] = dflt ? 0.0 : (1.0 - a) / 5.0 - 1.0 / 9.0;
+            rd.dA[k][2] = dflt ? 0.0 : (1.0 - a) / 20.0 - 1.0 / 36.0;
+            if (!dflt) rd.gen = 1;
+        }
+        h->gen = rd.gen != 0;   // alpha and m are options of the handle: the same for every run
         rd.gx = opt.body[0];
         rd.gy = opt.body[1];
         rd.rho_ref[0] = opt.rho_ref[0];
         rd.rho_ref[1] = opt.rho_ref[1];
         rd.thr = rho_bulk / 3.0;
+        sc::fill_coef_f32(rd);
         rd.init_kind = gr.init_kind;
         rd.row0 = (int)h->rows.size();
         rd.x_lo = gr.x_lo;
@@ -618,7 +655,7 @@ int fetch_fields(lbm_t* h, int run, double* a, double* b, int on_device, bool ve
     } else {
         sc::MomOut mo{da, db, rd.nx};
         const int W = h->tile_w;
-        e = dispatch(h->precision, [&](auto L) {
+        e = dispatch_step(h, [&](auto L) {
             return L.moments(W, h->d_runs, h->d_tiles + h->tile_begin[run], h->tile_count[run], (int)((h->t - 1) & 1),
                              mo, h->stream);
         });
@@ -647,6 +684,8 @@ void lbm_default_options(lbm_options* opt) {
     opt->tile_h = 4;
     opt->graph_chunk = 0;
     opt->rho_bulk = 2.0;
+    opt->alpha[0] = opt->alpha[1] = 4.0 / 9.0;
+    opt->molecular_mass[0] = opt->molecular_mass[1] = 1.0;
 }
 
 int lbm_create(const lbm_geometry* g, double G_AB, const double wall[2], double tau_A, double tau_B,
@@ -829,6 +868,10 @@ struct CkHeader {
     int64_t t, nlog;
     double rho_ref[2], rho_bulk, body[2];
 };
+// version 2 appends the species model after the header
+struct CkModel {
+    double alpha[2], molecular_mass[2];
+};
 struct CkRun {
     int32_t nx, ny, cap_x0, cap_x1, y_bot, y_top, has_mask, reserved;
     double G, GwA, GwB, tauA, tauB;
@@ -843,7 +886,7 @@ int lbm_save(lbm_t* h, const char* path) {
     CkHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, kMagic, 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.precision = h->precision;
     hd.nruns = h->nruns;
     hd.log_every = h->opt.log_every;
@@ -857,7 +900,12 @@ int lbm_save(lbm_t* h, const char* path) {
     hd.rho_bulk = h->runs[0].thr * 3.0;
     hd.body[0] = h->opt.body[0];
     hd.body[1] = h->opt.body[1];
-    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1;
+    CkModel md;
+    for (int k = 0; k < 2; ++k) {
+        md.alpha[k] = h->opt.alpha[k];
+        md.molecular_mass[k] = h->opt.molecular_mass[k];
+    }
+    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(&md, sizeof(md), 1, fp) == 1;
     std::vector<char> pops;
     for (int r = 0; r < h->nruns && ok; ++r) {
         const RunDesc& rd = h->runs[r];
@@ -906,8 +954,13 @@ int lbm_load(const char* path, const lbm_options* opt_in, lbm_t** out) {
     FILE* fp = fopen(path, "rb");
     if (!fp) return LBM_EIO;
     CkHeader hd;
-    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 ||
-        hd.nruns < 1 || hd.nruns > 65535) {
+    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, kMagic, 8) != 0 ||
+        (hd.version != 1 && hd.version != 2) || hd.nruns < 1 || hd.nruns > 65535) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    CkModel md = {{4.0 / 9.0, 4.0 / 9.0}, {1.0, 1.0}};   // version 1: the alpha = 4/9, m = 1 model
+    if (hd.version == 2 && fread(&md, sizeof(md), 1, fp) != 1) {
         fclose(fp);
         return LBM_EIO;
     }
@@ -948,6 +1001,10 @@ int lbm_load(const char* path, const lbm_options* opt_in, lbm_t** out) {
     opt.tile_w = hd.tile_w;
     opt.tile_h = hd.tile_h;
     opt.autotune = 0;
+    for (int k = 0; k < 2; ++k) {
+        opt.alpha[k] = md.alpha[k];
+        opt.molecular_mass[k] = md.molecular_mass[k];
+    }
     std::vector<lbm_geometry> g(hd.nruns);
     std::vector<double> G(hd.nruns), wall(2 * hd.nruns), tA(hd.nruns), tB(hd.nruns);
     for (int r = 0; r < hd.nruns; ++r) {

@@ -10,6 +10,14 @@
 
 namespace sc {
 
+// Step coefficients rounded to FP32 on the host: the FP32 and FP16S kernels
+// read these, so that no FP64 -> FP32 conversion runs at each CTA's start.
+struct CoefF32 {
+    float G, Gw[2], taum[2], itau[2], mitau[2], m[2], gx, gy;
+    float dA[2][3];
+    float sh[2][3];   // FP16S shift w_g rho_ref,k per direction group
+};
+
 // One run (one capillary) as the kernels see it.  Populations of buffer b:
 //   buf[b] + ((k * 9 + i) * ny + y) * pitch + x     (elements of the storage type)
 struct RunDesc {
@@ -20,6 +28,15 @@ struct RunDesc {
     const uint8_t* mask;      // device [ny][nx] or nullptr (analytic plates)
     // Eqs. 2, 7-11 parameters; itau = 1 / tau computed on the host in FP64
     double G, GwA, GwB, tauA, tauB, itauA, itauB, gx, gy;
+    // molecular masses m_k (rho_k = m_k n_k): the weights m_k / tau_k of U in
+    // Eq. 8 and the factors tau_k / m_k of the shift in Eq. 7, in FP64 on the host
+    double mA, mB, mitauA, mitauB, taumA, taumB;
+    // free rest fraction alpha_k of Eqs. 3-5: dA[k][g] = A_g(alpha_k) - w_g for
+    // the groups g = rest, axis, diagonal; gen = 0 when both alpha_k are 4/9
+    // and both m_k are 1 (the step kernels of the standard model run then)
+    double dA[2][3];
+    int gen;
+    CoefF32 c32;
     double rho_ref[2];        // FP16S shift per species
     double thr;               // precursor threshold rho_bulk / 3
     // initial layout
@@ -29,6 +46,32 @@ struct RunDesc {
     const double* init_nB;
     double* log;              // device ring [cap][6] of this run, or nullptr
 };
+
+// Fills rd.c32 from the FP64 fields (round to nearest, as a device conversion
+// would).  The FP16S shift stays w_g rho_ref for every alpha_k: it is only the
+// offset of the stored values, the same in the step and in the mass sums.
+inline void fill_coef_f32(RunDesc& rd) {
+    CoefF32& c = rd.c32;
+    c.G = (float)rd.G;
+    c.Gw[0] = (float)rd.GwA;
+    c.Gw[1] = (float)rd.GwB;
+    c.taum[0] = (float)rd.taumA;
+    c.taum[1] = (float)rd.taumB;
+    c.itau[0] = (float)rd.itauA;
+    c.itau[1] = (float)rd.itauB;
+    c.mitau[0] = (float)rd.mitauA;
+    c.mitau[1] = (float)rd.mitauB;
+    c.m[0] = (float)rd.mA;
+    c.m[1] = (float)rd.mB;
+    c.gx = (float)rd.gx;
+    c.gy = (float)rd.gy;
+    const float w[3] = {4.0f / 9.0f, 1.0f / 9.0f, 1.0f / 36.0f};
+    for (int k = 0; k < 2; ++k)
+        for (int g = 0; g < 3; ++g) {
+            c.dA[k][g] = (float)rd.dA[k][g];
+            c.sh[k][g] = w[g] * (float)rd.rho_ref[k];
+        }
+}
 
 // column chunks (CTAs) per row of the mass reduction
 constexpr int kMassChunks = 4;
@@ -59,9 +102,10 @@ struct LogCtl {
 
 enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
-template <typename S>
-struct Launch {
-    static cudaError_t init(const RunDesc* d_runs, int nruns, int max_nodes, cudaStream_t s);
+// Step kernels (one pass of Eq. 2 over every tile) and the moments pass.
+// GEN: the runs have some alpha_k != 4/9 or m_k != 1.
+template <typename S, bool GEN>
+struct Step {
     static cudaError_t step(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                             cudaStream_t s);
     static cudaError_t step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
@@ -84,6 +128,12 @@ struct Launch {
                                   cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
+};
+
+// Initialisation, observables, reductions and population transfers.
+template <typename S>
+struct Launch {
+    static cudaError_t init(const RunDesc* d_runs, int nruns, int max_nodes, cudaStream_t s);
     static cudaError_t densities(const RunDesc* d_runs, int run, int parity, int nodes, double* nA,
                                  double* nB, cudaStream_t s);
     static cudaError_t track(const RunDesc* d_runs, int nruns, int max_cap, int parity, int* first, LogCtl lc,
@@ -102,5 +152,11 @@ cudaError_t launch_log_advance(LogCtl lc, cudaStream_t s);
 extern template struct Launch<double>;
 extern template struct Launch<float>;
 extern template struct Launch<__half>;
+extern template struct Step<double, false>;
+extern template struct Step<double, true>;
+extern template struct Step<float, false>;
+extern template struct Step<float, true>;
+extern template struct Step<__half, false>;
+extern template struct Step<__half, true>;
 
 }  // namespace sc

@@ -13,9 +13,10 @@
 //   3. S_kbar = sum_{i=1..8} (w_i n_kbar(x + c_i)) c_i, i ascending (Eq. 9 with
 //      the w_i-weighted G, n = 0 on solids); Wl = sum_i (w_i s(x + c_i)) c_i
 //      (Eq. 11); a_k = (-(G S_kbar) - (G_kw Wl)) + g
-//   4. U = (j_A itau_A + j_B itau_B) / (n_A itau_A + n_B itau_B)     (Eq. 8)
-//   5. u_k = U + tau_k a_k                                               (Eq. 7)
+//   4. U = (j_A mt_A + j_B mt_B) / (n_A mt_A + n_B mt_B), mt_k = m_k / tau_k  (Eq. 8)
+//   5. u_k = U + tm_k a_k, tm_k = tau_k / m_k                            (Eq. 7)
 //   6. feq_i = (w_i n_k) (((1 + 3 cu) + 4.5 (cu cu)) - 1.5 usq)   (Eqs. 3-5)
+//      [+ dA_i n_k with dA_i = A_i(alpha_k) - w_i when alpha_k != 4/9]
 //   7. F'_i = ft_i - (ft_i - feq_i) itau_k                               (Eq. 2)
 //
 // Step kernel design (sm_103a, HBM-bound stencil, no tensor cores):
@@ -100,12 +101,8 @@ template <typename S> struct Shift {
 template <> struct Shift<__half> {
     float v[2][3];
     __device__ __forceinline__ void load(const RunDesc& rd) {
-        for (int k = 0; k < 2; ++k) {
-            float r = (float)rd.rho_ref[k];
-            v[k][0] = Wt<float>::w0 * r;
-            v[k][1] = Wt<float>::w1 * r;
-            v[k][2] = Wt<float>::w5 * r;
-        }
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < 3; ++g) v[k][g] = rd.c32.sh[k][g];
     }
 };
 __device__ __forceinline__ constexpr int grp(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
@@ -214,23 +211,60 @@ __device__ __forceinline__ RowIdx rows_of(int r, int ny) {
     return q;
 }
 
-// Per-CTA constants of the step.
-template <typename S>
+// Per-CTA constants of the step.  GEN: the run has some alpha_k != 4/9 or
+// m_k != 1 (a separate instantiation of every step kernel, so that the
+// standard model carries neither the extra coefficients nor their registers).
+template <typename S, bool GEN>
 struct StepCtx {
     using C = typename Prec<S>::C;
-    C G, Gw[2], tau[2], itau[2], gx, gy;
+    C G, Gw[2], taum[2], itau[2], mitau[2], m[2], gx, gy;
+    C dA[2][3];   // A_g(alpha_k) - w_g (GEN only; 0 for a species with alpha_k = 4/9)
     Shift<S> sh;
+    // With m_k = 1 (not GEN), taum = tau and the weights of U are itau.
+    __device__ __forceinline__ const C (&wU() const)[2] {
+        if constexpr (GEN) return mitau;
+        else return itau;
+    }
     __device__ __forceinline__ void load(const RunDesc& rd) {
         sh.load(rd);
-        G = (C)rd.G;
-        Gw[0] = (C)rd.GwA;
-        Gw[1] = (C)rd.GwB;
-        tau[0] = (C)rd.tauA;
-        tau[1] = (C)rd.tauB;
-        itau[0] = (C)rd.itauA;
-        itau[1] = (C)rd.itauB;
-        gx = (C)rd.gx;
-        gy = (C)rd.gy;
+        if constexpr (sizeof(C) == 4) {
+            const CoefF32& c = rd.c32;
+            G = c.G;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                Gw[k] = c.Gw[k];
+                taum[k] = c.taum[k];
+                itau[k] = c.itau[k];
+                if constexpr (GEN) {
+                    mitau[k] = c.mitau[k];
+                    m[k] = c.m[k];
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) dA[k][g] = c.dA[k][g];
+                }
+            }
+            gx = c.gx;
+            gy = c.gy;
+        } else {
+            G = (C)rd.G;
+            Gw[0] = (C)rd.GwA;
+            Gw[1] = (C)rd.GwB;
+            taum[0] = (C)rd.taumA;
+            taum[1] = (C)rd.taumB;
+            itau[0] = (C)rd.itauA;
+            itau[1] = (C)rd.itauB;
+            gx = (C)rd.gx;
+            gy = (C)rd.gy;
+            if constexpr (GEN) {
+                mitau[0] = (C)rd.mitauA;
+                mitau[1] = (C)rd.mitauB;
+                m[0] = (C)rd.mA;
+                m[1] = (C)rd.mB;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) dA[k][g] = (C)rd.dA[k][g];
+            }
+        }
     }
 };
 
@@ -247,8 +281,8 @@ struct NodeState {
     C n[2], jx[2], jy[2], ax[2], ay[2];
 };
 
-template <typename S, int W>
-__device__ __forceinline__ void node_state(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+template <typename S, int W, bool G>
+__device__ __forceinline__ void node_state(const StepCtx<S, G>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
                                            const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
                                            NodeState<S>& ns) {
     using C = typename Prec<S>::C;
@@ -296,16 +330,18 @@ __device__ __forceinline__ void node_state(const StepCtx<S>& cx, const typename 
 }
 
 // Steps 4-7: common velocity, shifted equilibria and BGK relaxation.
-template <typename S>
-__device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9],
-                                      const NodeState<S>& ns, typename Prec<S>::C (&fnew)[2][9]) {
+// GEN: the equilibria carry dA_i n_k and U weighs m_k / tau_k.
+template <typename S, bool GEN>
+__device__ __forceinline__ void relax(const StepCtx<S, GEN>& cx, const typename Prec<S>::C (&fc)[2][9],
+                                           const NodeState<S>& ns, typename Prec<S>::C (&fnew)[2][9]) {
     using C = typename Prec<S>::C;
     using Wc = Wt<C>;
     using A = Ar<C>;
     // common velocity (Eq. 8) and shifted equilibrium velocities (Eq. 7)
-    const C den = A::fma(ns.n[0], cx.itau[0], A::mul(ns.n[1], cx.itau[1]));
-    const C numx = A::fma(ns.jx[0], cx.itau[0], A::mul(ns.jx[1], cx.itau[1]));
-    const C numy = A::fma(ns.jy[0], cx.itau[0], A::mul(ns.jy[1], cx.itau[1]));
+    const C(&wu)[2] = cx.wU();
+    const C den = A::fma(ns.n[0], wu[0], A::mul(ns.n[1], wu[1]));
+    const C numx = A::fma(ns.jx[0], wu[0], A::mul(ns.jx[1], wu[1]));
+    const C numy = A::fma(ns.jy[0], wu[0], A::mul(ns.jy[1], wu[1]));
     C Ux, Uy;
     if constexpr (kCanonical<C>) {
         Ux = A::div(numx, den);
@@ -317,8 +353,8 @@ __device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const C ux = A::fma(cx.tau[k], ns.ax[k], Ux);
-        const C uy = A::fma(cx.tau[k], ns.ay[k], Uy);
+        const C ux = A::fma(cx.taum[k], ns.ax[k], Ux);
+        const C uy = A::fma(cx.taum[k], ns.ay[k], Uy);
         const C usq = A::fma(ux, ux, A::mul(uy, uy));
         const C b = A::mul(C(1.5), usq);
         const C nk = ns.n[k];
@@ -330,7 +366,8 @@ __device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<
                 const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
                 const C c = cu[i];
                 // Eqs. 3-5: wn (((1 + 3 c) + 4.5 (c c)) - b)
-                const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
+                C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(c, c), A::fma(C(3), c, C(1))), b));
+                if constexpr (GEN) feq = A::add(feq, A::mul(cx.dA[k][grp(i)], nk));   // free alpha_k
                 const C f = fc[k][i];
                 fnew[k][i] = A::fma(-A::sub(f, feq), cx.itau[k], f);   // Eq. 2: f - (f - feq) / tau
             }
@@ -346,7 +383,8 @@ __device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<
             for (int q = 0; q < 4; ++q) {
                 const C wn = q < 2 ? wn1 : wn5;
                 const C c = cp[q];
-                const C sy = A::mul(wn, A::fma(C(4.5), A::mul(c, c), base));
+                C sy = A::mul(wn, A::fma(C(4.5), A::mul(c, c), base));
+                if constexpr (GEN) sy = A::fma(cx.dA[k][q < 2 ? 1 : 2], nk, sy);   // free alpha_k
                 const C an = A::mul(A::mul(C(3), wn), c);
                 fnew[k][ia[q]] = A::fma(A::add(sy, an), it, A::mul(fc[k][ia[q]], om));
                 fnew[k][ib[q]] = A::fma(A::sub(sy, an), it, A::mul(fc[k][ib[q]], om));
@@ -364,13 +402,13 @@ __device__ __forceinline__ void relax(const StepCtx<S>& cx, const typename Prec<
 // strip): densities of this and the neighbouring nodes come from the shared
 // ring (slots of rows r-1, r, r+1), the node's pulled populations from fc.
 // MODE 0 writes the post-collision populations, MODE 1 the whole-fluid
-// velocity rho u = sum_k j_k + (1/2) sum_k n_k a_k.
+// velocity rho u = sum_k m_k j_k + (1/2) sum_k n_k a_k, rho = sum_k m_k n_k.
 // Populations of columns 0, 1 and nx - 2, nx - 1 are also written to their
 // periodic images at x = nx, nx + 1 and x = -2, -1 (ghost columns), so that
 // every source row a later step reads is one contiguous window; gr / gl give
 // the offsets of those images from the node (0 = none).
-template <typename S, int W, int MODE, bool GH = true>
-__device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+template <typename S, int W, int MODE, bool GH, bool G>
+__device__ __forceinline__ void collide_node(const StepCtx<S, G>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
                                              const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
                                              S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
                                              long long mo_idx, int gr = 0, int gl = 0) {
@@ -379,11 +417,20 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
     NodeState<S> ns;
     node_state<S, W>(cx, fc, m, sd, s_m, s_0, s_p, t, ns);
     if (MODE == 1) {
-        const C ntot = A::add(ns.n[0], ns.n[1]);
+        C rho, px, py;
+        if constexpr (G) {
+            rho = A::fma(cx.m[0], ns.n[0], A::mul(cx.m[1], ns.n[1]));
+            px = A::fma(cx.m[0], ns.jx[0], A::mul(cx.m[1], ns.jx[1]));
+            py = A::fma(cx.m[0], ns.jy[0], A::mul(cx.m[1], ns.jy[1]));
+        } else {   // m_k = 1
+            rho = A::add(ns.n[0], ns.n[1]);
+            px = A::add(ns.jx[0], ns.jx[1]);
+            py = A::add(ns.jy[0], ns.jy[1]);
+        }
         const C fxs = A::fma(ns.n[0], ns.ax[0], A::mul(ns.n[1], ns.ax[1]));
         const C fys = A::fma(ns.n[0], ns.ay[0], A::mul(ns.n[1], ns.ay[1]));
-        mo.ux[mo_idx] = (double)A::div(A::fma(C(0.5), fxs, A::add(ns.jx[0], ns.jx[1])), ntot);
-        mo.uy[mo_idx] = (double)A::div(A::fma(C(0.5), fys, A::add(ns.jy[0], ns.jy[1])), ntot);
+        mo.ux[mo_idx] = (double)A::div(A::fma(C(0.5), fxs, px), rho);
+        mo.uy[mo_idx] = (double)A::div(A::fma(C(0.5), fys, py), rho);
         return;
     }
     C fnew[2][9];
@@ -405,8 +452,8 @@ __device__ __forceinline__ void collide_node(const StepCtx<S>& cx, const typenam
 }
 
 // Dispatch: the ghost-writing variant only for the edge columns.
-template <typename S, int W, int MODE>
-__device__ __forceinline__ void collide_any(const StepCtx<S>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
+template <typename S, int W, int MODE, bool G>
+__device__ __forceinline__ void collide_any(const StepCtx<S, G>& cx, const typename Prec<S>::C (&fc)[2][9], unsigned m,
                                             const typename Prec<S>::C (*sd)[2][W], int s_m, int s_0, int s_p, int t,
                                             S* __restrict__ dst, unsigned plane, unsigned o, MomOut mo,
                                             long long mo_idx, int gr, int gl) {
@@ -466,7 +513,7 @@ struct RowPrefetch {
     }
 };
 
-template <typename S, int W, int MODE, bool L2PF = false>
+template <typename S, int W, int MODE, bool L2PF, bool G>
 __global__ void __launch_bounds__(W, (kMinBlocks<S, W>)) k_step(const RunDesc* __restrict__ runs,
                                                               const Tile* __restrict__ tiles, int parity, MomOut mo) {
     using C = typename Prec<S>::C;
@@ -479,7 +526,7 @@ __global__ void __launch_bounds__(W, (kMinBlocks<S, W>)) k_step(const RunDesc* _
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const StripCols sc(tl.x0, nx, W, t);
@@ -556,8 +603,8 @@ __global__ void __launch_bounds__(W, (kMinBlocks<S, W>)) k_step(const RunDesc* _
 // double-buffered row of momenta j_k for the common velocity.  One
 // __syncthreads per row.  The arithmetic per node is that of collide_node,
 // done by the thread of each species for its own populations.
-template <typename S, int W, bool GH>
-__device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, const typename Prec<S>::C (&f)[9],
+template <typename S, int W, bool GH, bool GEN>
+__device__ __forceinline__ void collide_species(const StepCtx<S, GEN>& cx, int k, const typename Prec<S>::C (&f)[9],
                                                 unsigned m, const typename Prec<S>::C (*sd)[2][W],
                                                 const typename Prec<S>::C (*jb)[W], int s_m, int s_0, int s_p, int c,
                                                 S* __restrict__ dst, unsigned plane, unsigned o, int gr, int gl) {
@@ -592,9 +639,10 @@ __device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, con
     Sy = A::fma(-Wc::w5, n8, Sy);
     const C ax = A::add(A::sub(-A::mul(cx.G, Sx), A::mul(cx.Gw[k], Wx)), cx.gx);
     const C ay = A::add(A::sub(-A::mul(cx.G, Sy), A::mul(cx.Gw[k], Wy)), cx.gy);
-    const C den = A::fma(nA, cx.itau[0], A::mul(nB, cx.itau[1]));
-    const C numx = A::fma(jxA, cx.itau[0], A::mul(jxB, cx.itau[1]));
-    const C numy = A::fma(jyA, cx.itau[0], A::mul(jyB, cx.itau[1]));
+    const C(&wu)[2] = cx.wU();
+    const C den = A::fma(nA, wu[0], A::mul(nB, wu[1]));
+    const C numx = A::fma(jxA, wu[0], A::mul(jxB, wu[1]));
+    const C numy = A::fma(jyA, wu[0], A::mul(jyB, wu[1]));
     C Ux, Uy;
     if constexpr (kCanonical<C>) {
         Ux = A::div(numx, den);
@@ -605,8 +653,8 @@ __device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, con
         Uy = A::mul(numy, rden);
     }
     const C n = k == 0 ? nA : nB;
-    const C ux = A::fma(cx.tau[k], ax, Ux);
-    const C uy = A::fma(cx.tau[k], ay, Uy);
+    const C ux = A::fma(cx.taum[k], ax, Ux);
+    const C uy = A::fma(cx.taum[k], ay, Uy);
     const C usq = A::fma(ux, ux, A::mul(uy, uy));
     const C b = A::mul(C(1.5), usq);
     const C wn0 = A::mul(Wc::w0, n), wn1 = A::mul(Wc::w1, n), wn5 = A::mul(Wc::w5, n);
@@ -617,7 +665,8 @@ __device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, con
         for (int i = 0; i < 9; ++i) {
             const C wn = i == 0 ? wn0 : (i <= 4 ? wn1 : wn5);
             const C cc = cu[i];
-            const C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(cc, cc), A::fma(C(3), cc, C(1))), b));
+            C feq = A::mul(wn, A::sub(A::fma(C(4.5), A::mul(cc, cc), A::fma(C(3), cc, C(1))), b));
+            if constexpr (GEN) feq = A::add(feq, A::mul(cx.dA[k][grp(i)], n));
             fnew[i] = A::fma(-A::sub(f[i], feq), cx.itau[k], f[i]);
         }
     } else {
@@ -630,7 +679,8 @@ __device__ __forceinline__ void collide_species(const StepCtx<S>& cx, int k, con
         for (int q = 0; q < 4; ++q) {
             const C wn = q < 2 ? wn1 : wn5;
             const C cc = cp[q];
-            const C sy = A::mul(wn, A::fma(C(4.5), A::mul(cc, cc), base));
+            C sy = A::mul(wn, A::fma(C(4.5), A::mul(cc, cc), base));
+            if constexpr (GEN) sy = A::fma(cx.dA[k][q < 2 ? 1 : 2], n, sy);
             const C an = A::mul(A::mul(C(3), wn), cc);
             fnew[ia[q]] = A::fma(A::add(sy, an), it, A::mul(f[ia[q]], om));
             fnew[ib[q]] = A::fma(A::sub(sy, an), it, A::mul(f[ib[q]], om));
@@ -683,7 +733,7 @@ __device__ __forceinline__ void pull_species(const S* __restrict__ p, unsigned p
 template <typename S, int W>
 constexpr int kSplitMinBlocks = (sizeof(typename Prec<S>::C) == 8 || 2 * W >= 1024) ? 1 : 1024 / (2 * W);
 
-template <typename S, int W>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(const RunDesc* __restrict__ runs,
                                                                               const Tile* __restrict__ tiles,
                                                                               int parity) {
@@ -700,7 +750,7 @@ __global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(c
     const int k = threadIdx.x / W, c = threadIdx.x % W;
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]) + (unsigned)(k * 9) * (unsigned)plane;
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const C sh0 = cx.sh.v[k][0], sh1 = cx.sh.v[k][1], sh2 = cx.sh.v[k][2];
     const StripCols sc(tl.x0, nx, W, c);
@@ -761,7 +811,7 @@ __global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(c
 template <typename S, int W>
 constexpr int kSmemMinBlocks = (sizeof(typename Prec<S>::C) == 8 || W >= 1024) ? 1 : 1024 / W;
 
-template <typename S, int W>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const RunDesc* __restrict__ runs,
                                                                         const Tile* __restrict__ tiles,
                                                                         int parity) {
@@ -776,7 +826,7 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const StripCols sc(tl.x0, nx, W, t);
@@ -842,7 +892,7 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
 template <typename S, int W>
 constexpr int kBidirMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 512 / W;   // 64 registers
 
-template <typename S, int W>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(const RunDesc* __restrict__ runs,
                                                                               const Tile* __restrict__ tiles,
                                                                               int parity) {
@@ -857,7 +907,7 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x % W, grp_d = threadIdx.x / W;   // grp_d 0: up (U), 1: down (D)
     const StripCols sc(tl.x0, nx, W, t);
@@ -975,7 +1025,7 @@ template <> struct Pair<__half> {
 template <typename S, int W>
 constexpr int kPairMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : (W >= 128 ? 5 : 8);
 
-template <typename S, int W>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(W, (kPairMinBlocks<S, W>)) k_step_pair(const RunDesc* __restrict__ runs,
                                                                         const Tile* __restrict__ tiles, int parity) {
     using C = typename Prec<S>::C;
@@ -990,7 +1040,7 @@ __global__ void __launch_bounds__(W, (kPairMinBlocks<S, W>)) k_step_pair(const R
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const int x0 = tl.x0;
@@ -1151,7 +1201,7 @@ __global__ void __launch_bounds__(W, (kPairMinBlocks<S, W>)) k_step_pair(const R
 template <typename S, int W, int TY>
 constexpr int kTileMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 1024 / (W * TY);   // 64 registers
 
-template <typename S, int W, int TY>
+template <typename S, int W, int TY, bool G>
 __global__ void __launch_bounds__(W * TY, (kTileMinBlocks<S, W, TY>)) k_step_tile(const RunDesc* __restrict__ runs,
                                                                                 const Tile* __restrict__ tiles,
                                                                                 int parity) {
@@ -1167,7 +1217,7 @@ __global__ void __launch_bounds__(W * TY, (kTileMinBlocks<S, W, TY>)) k_step_til
     const int x = tl.x0 - 1 + tx;                          // unwrapped column, in [-1, nx] when active
     const int r = tl.y0 - 1 + ty;                          // unwrapped row, in [-1, ny] when active
     const bool act = x <= min(tl.x0 + W - 2, nx) && r <= tl.y1;
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const RowIdx q = rows_of(act ? r : 0, ny);
     const int xw = x < 0 ? x + nx : (x >= nx ? x - nx : x);
@@ -1244,7 +1294,7 @@ __device__ __forceinline__ void issue_pull(const S* __restrict__ src, unsigned p
 template <typename S, int W>
 constexpr int kPipeMinBlocks = (sizeof(typename Prec<S>::C) == 8 || W >= 768) ? 1 : 768 / W;   // <= 85 registers
 
-template <typename S, int W>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(W, (kPipeMinBlocks<S, W>)) k_step_pf(const RunDesc* __restrict__ runs,
                                                                       const Tile* __restrict__ tiles, int parity) {
     using C = typename Prec<S>::C;
@@ -1258,7 +1308,7 @@ __global__ void __launch_bounds__(W, (kPipeMinBlocks<S, W>)) k_step_pf(const Run
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const StripCols sc(tl.x0, nx, W, t);
@@ -1354,7 +1404,7 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename S, int W, int D>
+template <typename S, int W, int D, bool G>
 __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
                                                   int parity) {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
@@ -1370,7 +1420,7 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const StripCols sc(tl.x0, nx, W, t);
@@ -1561,7 +1611,7 @@ __device__ __forceinline__ void pull_slot_bb(const S* P, unsigned m, const Shift
             if (SOL(m, -cyo(i), -cxo(i))) f[k][i] = dec(ldg(gown + (unsigned)(9 * k + opp(i)) * plane), sh.v[k][grp(i)]);
 }
 
-template <typename S, int W, int D>
+template <typename S, int W, int D, bool G>
 __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs, const Tile* __restrict__ tiles,
                                                 int parity, uint32_t* __restrict__ err) {
     using C = typename Prec<S>::C;
@@ -1579,7 +1629,7 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);
-    StepCtx<S> cx;
+    StepCtx<S, G> cx;
     cx.load(rd);
     const int t = threadIdx.x;
     const int x0 = tl.x0, y0 = tl.y0, y1 = tl.y1;
@@ -1705,7 +1755,7 @@ constexpr size_t async_smem_bytes() {
     return (size_t)D * 18 * W * sizeof(S) + 4 * 2 * W * sizeof(typename Prec<S>::C);
 }
 
-// ---- initial state: f_i = f_i^eq(n^0, u = 0) = w_i n^0 on fluid nodes -----
+// ---- initial state: f_i = f_i^eq(n^0, u = 0) = A_i n^0 on fluid nodes -----
 template <typename S>
 __global__ void k_init(const RunDesc* __restrict__ runs) {
     using C = typename Prec<S>::C;
@@ -1743,6 +1793,8 @@ __global__ void k_init(const RunDesc* __restrict__ runs) {
                 const C n = (C)n0[k];
                 for (int i = 0; i < 9; ++i) {
                     const C w = i == 0 ? Wc::w0 : (i <= 4 ? Wc::w1 : Wc::w5);
+                    C feq = Ar<C>::mul(w, n);
+                    if (rd.gen) feq = Ar<C>::add(feq, Ar<C>::mul((C)rd.dA[k][grp(i)], n));
                     S* p = base + ((long long)k * 9 + i) * rd.plane + o;
                     const int gr = ghost_r(x, rd.nx), gl = ghost_l(x, rd.nx);
                     if (sol) {
@@ -1750,9 +1802,9 @@ __global__ void k_init(const RunDesc* __restrict__ runs) {
                         if (gr) p[gr] = S(0.0f);
                         if (gl) p[gl] = S(0.0f);
                     } else {
-                        enc(p, w * n, sh.v[k][grp(i)]);
-                        if (gr) enc(p + gr, w * n, sh.v[k][grp(i)]);
-                        if (gl) enc(p + gl, w * n, sh.v[k][grp(i)]);
+                        enc(p, feq, sh.v[k][grp(i)]);
+                        if (gr) enc(p + gr, feq, sh.v[k][grp(i)]);
+                        if (gl) enc(p + gl, feq, sh.v[k][grp(i)]);
                     }
                 }
             }

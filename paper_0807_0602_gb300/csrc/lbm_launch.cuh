@@ -35,32 +35,32 @@ cudaError_t Launch<S>::init(const RunDesc* d_runs, int nruns, int max_nodes, cud
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                             cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     MomOut none{nullptr, nullptr, 0};
     switch (W) {
-        case 64: k_step<S, 64, 0><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
-        case 128: k_step<S, 128, 0><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
-        case 256: k_step<S, 256, 0><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 64: k_step<S, 64, 0, false, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 128: k_step<S, 128, 0, false, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 256: k_step<S, 256, 0, false, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S, int W, int D>
+template <typename S, int W, int D, bool G>
 static cudaError_t launch_async(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, cudaStream_t s) {
     constexpr size_t smem = async_smem_bytes<S, W, D>();
     static std::atomic<unsigned long long> configured{0};   // per instantiation, one bit per device
-    const cudaError_t e = ensure_dynamic_smem((const void*)k_step_async<S, W, D>, (int)smem, configured);
+    const cudaError_t e = ensure_dynamic_smem((const void*)k_step_async<S, W, D, G>, (int)smem, configured);
     if (e != cudaSuccess) return e;
-    k_step_async<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity);
+    k_step_async<S, W, D, G><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity);
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_async(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if constexpr (sizeof(S) == 2) {
@@ -68,18 +68,18 @@ cudaError_t Launch<S>::step_async(int W, int D, const RunDesc* d_runs, const Til
     } else {
         const int key = W * 10 + D;
         switch (key) {
-            case 643: return launch_async<S, 64, 3>(d_runs, d_tiles, ntiles, parity, s);
-            case 644: return launch_async<S, 64, 4>(d_runs, d_tiles, ntiles, parity, s);
-            case 1283: return launch_async<S, 128, 3>(d_runs, d_tiles, ntiles, parity, s);
-            case 1284: return launch_async<S, 128, 4>(d_runs, d_tiles, ntiles, parity, s);
-            case 2563: return launch_async<S, 256, 3>(d_runs, d_tiles, ntiles, parity, s);
-            case 2564: return launch_async<S, 256, 4>(d_runs, d_tiles, ntiles, parity, s);
+            case 643: return launch_async<S, 64, 3, G>(d_runs, d_tiles, ntiles, parity, s);
+            case 644: return launch_async<S, 64, 4, G>(d_runs, d_tiles, ntiles, parity, s);
+            case 1283: return launch_async<S, 128, 3, G>(d_runs, d_tiles, ntiles, parity, s);
+            case 1284: return launch_async<S, 128, 4, G>(d_runs, d_tiles, ntiles, parity, s);
+            case 2563: return launch_async<S, 256, 3, G>(d_runs, d_tiles, ntiles, parity, s);
+            case 2564: return launch_async<S, 256, 4, G>(d_runs, d_tiles, ntiles, parity, s);
             default: return cudaErrorInvalidValue;
         }
     }
 }
 
-template <typename S, int W, int D>
+template <typename S, int W, int D, bool G>
 static cudaError_t launch_tma(const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity, uint32_t* err,
                               cudaStream_t s) {
     constexpr size_t smem = TmaGeom<S, W, D>::smem_bytes();
@@ -87,39 +87,39 @@ static cudaError_t launch_tma(const RunDesc* d_runs, const Tile* d_tiles, int nt
         return cudaErrorInvalidValue;
     } else {
         static std::atomic<unsigned long long> configured{0};   // per instantiation, one bit per device
-        const cudaError_t e = ensure_dynamic_smem((const void*)k_step_tma<S, W, D>, (int)smem, configured);
+        const cudaError_t e = ensure_dynamic_smem((const void*)k_step_tma<S, W, D, G>, (int)smem, configured);
         if (e != cudaSuccess) return e;
-        k_step_tma<S, W, D><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
+        k_step_tma<S, W, D, G><<<ntiles, W, smem, s>>>(d_runs, d_tiles, parity, err);
         return cudaGetLastError();
     }
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_tma(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_tma(int W, int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                 uint32_t* err, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W * 10 + D) {
-        case 644: return launch_tma<S, 64, 4>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 646: return launch_tma<S, 64, 6>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 648: return launch_tma<S, 64, 8>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 1284: return launch_tma<S, 128, 4>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 1286: return launch_tma<S, 128, 6>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 1288: return launch_tma<S, 128, 8>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 2564: return launch_tma<S, 256, 4>(d_runs, d_tiles, ntiles, parity, err, s);
-        case 2566: return launch_tma<S, 256, 6>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 644: return launch_tma<S, 64, 4, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 646: return launch_tma<S, 64, 6, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 648: return launch_tma<S, 64, 8, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1284: return launch_tma<S, 128, 4, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1286: return launch_tma<S, 128, 6, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 1288: return launch_tma<S, 128, 8, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 2564: return launch_tma<S, 256, 4, G>(d_runs, d_tiles, ntiles, parity, err, s);
+        case 2566: return launch_tma<S, 256, 6, G>(d_runs, d_tiles, ntiles, parity, err, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step_pf<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 64: k_step_pf<S, 64, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
         case 128:
             if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
-            else k_step_pf<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
+            else k_step_pf<S, 128, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
             break;
 
         default: return cudaErrorInvalidValue;
@@ -127,103 +127,103 @@ cudaError_t Launch<S>::step_pf(int W, const RunDesc* d_runs, const Tile* d_tiles
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_split(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_split(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step_split<S, 64><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 128: k_step_split<S, 128><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 256: k_step_split<S, 256><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 64: k_step_split<S, 64, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128: k_step_split<S, 128, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 256: k_step_split<S, 256, G><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_l2pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_l2pf(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     MomOut none{nullptr, nullptr, 0};
     switch (W) {
-        case 64: k_step<S, 64, 0, true><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
-        case 128: k_step<S, 128, 0, true><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
-        case 256: k_step<S, 256, 0, true><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 64: k_step<S, 64, 0, true, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 128: k_step<S, 128, 0, true, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, none); break;
+        case 256: k_step<S, 256, 0, true, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, none); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_smem(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_smem(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step_smem<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 128: k_step_smem<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 64: k_step_smem<S, 64, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 128: k_step_smem<S, 128, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
         case 256:
             if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
-            else k_step_smem<S, 256><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
+            else k_step_smem<S, 256, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
             break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_pair(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_pair(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step_pair<S, 64><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 64: k_step_pair<S, 64, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity); break;
         case 128:
             if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
-            else k_step_pair<S, 128><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
+            else k_step_pair<S, 128, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
             break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     // R = collided rows per tile: TY = R + 2 thread rows
     switch (W * 100 + R) {
-        case 3206: k_step_tile<S, 32, 8><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 3214: k_step_tile<S, 32, 16><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 3230: k_step_tile<S, 32, 32><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 6406: k_step_tile<S, 64, 8><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
-        case 6414: k_step_tile<S, 64, 16><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 3206: k_step_tile<S, 32, 8, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 3214: k_step_tile<S, 32, 16, G><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 3230: k_step_tile<S, 32, 32, G><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 6406: k_step_tile<S, 64, 8, G><<<ntiles, 512, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 6414: k_step_tile<S, 64, 16, G><<<ntiles, 1024, 0, s>>>(d_runs, d_tiles, parity); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                   cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step_bidir<S, 64><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
+        case 64: k_step_bidir<S, 64, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
         case 128:
             if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
-            else k_step_bidir<S, 128><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
+            else k_step_bidir<S, 128, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
             break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename S>
-cudaError_t Launch<S>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+template <typename S, bool G>
+cudaError_t Step<S, G>::moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64: k_step<S, 64, 1><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, out); break;
-        case 128: k_step<S, 128, 1><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, out); break;
-        case 256: k_step<S, 256, 1><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        case 64: k_step<S, 64, 1, false, G><<<ntiles, 64, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        case 128: k_step<S, 128, 1, false, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity, out); break;
+        case 256: k_step<S, 256, 1, false, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity, out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

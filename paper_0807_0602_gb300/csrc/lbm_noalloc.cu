@@ -87,6 +87,7 @@ extern "C" int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void
     rd.y_top = g->y_top;
     rd.rho_ref[0] = rho_ref ? rho_ref[0] : 0.0;
     rd.rho_ref[1] = rho_ref ? rho_ref[1] : 0.0;
+    sc::fill_coef_f32(rd);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (precision) {
         case LBM_F64: k_rows_noalloc<double><<<g->ny, sc::kMassThreads, 0, s>>>(rd, part); break;

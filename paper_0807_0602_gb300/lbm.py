@@ -77,7 +77,8 @@ class Lattice:
 
     ``runs``: a run dict or a list of them, each with ``geom`` (nx, ny,
     cap_x0, cap_x1, y_bot, y_top, optional mask), ``params`` (G, G_Aw, G_Bw,
-    tau_A, tau_B; optional body, rho_bulk) and ``init`` (("slab", x_lo, x_hi),
+    tau_A, tau_B; optional body, rho_bulk, alpha = (alpha_A, alpha_B) of
+    Eqs. 3-5 and mass = (m_A, m_B), shared by all runs) and ``init`` (("slab", x_lo, x_hi),
     ("droplet", cx, cy, r) or ("fields", nA, nB)).
     """
 
@@ -107,6 +108,10 @@ class Lattice:
         self.runs = list(runs)
         # with an explicit kernel the tiling is set together with it after creation
         # (the creation options only know the default kernel's tilings)
+        species = [(tuple(r["params"].get("alpha", (4.0 / 9.0,) * 2)), tuple(r["params"].get("mass", (1.0, 1.0))))
+                   for r in self.runs]
+        if any(sp != species[0] for sp in species):
+            raise ValueError("alpha and mass are options of the handle: every run must give the same values")
         opt = self._options(self.runs[0]["params"], log_every, log_capacity, autotune,
                             tile if kernel is None else (0, 0), graph_chunk, rho_ref)
         keep = []
@@ -141,6 +146,10 @@ class Lattice:
         opt.rho_bulk = float(prm.get("rho_bulk", 2.0))
         body = prm.get("body", (0.0, 0.0))
         opt.body[0], opt.body[1] = float(body[0]), float(body[1])
+        alpha = prm.get("alpha", (4.0 / 9.0, 4.0 / 9.0))
+        mass = prm.get("mass", (1.0, 1.0))
+        opt.alpha[0], opt.alpha[1] = float(alpha[0]), float(alpha[1])
+        opt.molecular_mass[0], opt.molecular_mass[1] = float(mass[0]), float(mass[1])
         if self._alloc is not None:
             opt.alloc, opt.free = self._alloc.alloc, self._alloc.free
         opt.stream = ctypes.c_void_p(int(self.stream.cuda_stream))

@@ -99,6 +99,14 @@ def test_invalid_arguments_are_rejected_without_touching_the_gpu(lib):
     opt.tile_w = 128
     opt.log_every, opt.log_capacity = 10, 0
     assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
+    opt.log_every = 0
+    for alpha in (1.0, -0.1, math.nan):                              # Eqs. 3-5: 0 <= alpha < 1
+        opt.alpha[1] = alpha
+        assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
+    opt.alpha[1] = 4.0 / 9.0
+    for m in (0.0, -1.0, math.inf):                                  # rho_k = m_k n_k, m_k > 0
+        opt.molecular_mass[0] = m
+        assert _create(lib, _geom(), opt=opt)[0] == L.LBM_EINVAL
 
 
 def test_stream_probe_rejects_invalid_arguments_without_launching(lib):
@@ -133,12 +141,13 @@ def test_default_options(lib):
     opt = L.Options()
     lib.lbm_default_options(ctypes.byref(opt))
     assert opt.precision == L.LBM_F32 and opt.tile_w == 128 and opt.tile_h == 4 and opt.rho_bulk == 2.0
+    assert list(opt.alpha) == [4.0 / 9.0] * 2 and list(opt.molecular_mass) == [1.0, 1.0]
 
 
 def test_structure_layouts_match_header():
     from paper_0807_0602_gb300 import _lib as L
     # 8 int32 + pointer + 7 doubles + 2 pointers
     assert ctypes.sizeof(L.Geometry) == 8 * 4 + 8 + 7 * 8 + 2 * 8
-    # 8 int32 + 5 doubles + 4 pointers
-    assert ctypes.sizeof(L.Options) == 8 * 4 + 5 * 8 + 4 * 8
+    # 8 int32 + 5 doubles + 4 pointers + 4 doubles
+    assert ctypes.sizeof(L.Options) == 8 * 4 + 5 * 8 + 4 * 8 + 4 * 8
     assert ctypes.sizeof(L.RunInfo) == 6 * 4 + 8 + 2 * 8
