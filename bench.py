@@ -48,13 +48,18 @@ KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
                 "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir"]
 # committed ncu summaries of the step kernel on this workload, by (variant, tile)
+# keyed by (kernel, tile, species): species None for alpha = 4/9, m = 1, else --species
+SPECIES_1_3 = (4.0 / 9.0, 0.8, 1.0, 25.0 / 9.0)
 PROFILES = {
-    (6, (128, 4)): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
-    (6, (64, 4)): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
-    (9, (64, 8)): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
+    (6, (128, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
+    (6, (64, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 8), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
+    (9, (64, 8), SPECIES_1_3): os.path.join(ROOT, "profiles",
+                                            "k_step_bidir_species_tile64x8_f32_capillary_8192x160.txt"),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
-                  for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "lbm_device.h")]
+                  for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "kernels_gen_f32.cu",
+                            "lbm_device.h")]
 
 
 # (alpha_A, alpha_B, m_A, m_B) of --species, or None for alpha = 4/9, m = 1
@@ -81,8 +86,8 @@ def read_traffic(kvar: int, tile):
     """DRAM bytes per step-kernel launch from the committed ncu summary of
     this kernel variant and tile, or None if there is none or the kernel
     sources changed since the counters were taken."""
-    key = (int(kvar), (int(tile[0]), int(tile[1])))
-    if key not in PROFILES or SPECIES is not None:   # the summaries cover the alpha = 4/9, m = 1 kernels
+    key = (int(kvar), (int(tile[0]), int(tile[1])), SPECIES)
+    if key not in PROFILES:
         return None
     try:
         kv = {}
