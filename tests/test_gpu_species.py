@@ -175,3 +175,33 @@ def test_flat_interface_pressure_balance_fp32():
     assert abs(pA - pB) <= 1e-4 * pA
     qA, qB = oracle.pressure(a[0, 28], b[0, 28], G), oracle.pressure(a[0, 52], b[0, 52], G)
     assert abs(qA - qB) > 0.1 * qA
+
+
+def test_laplace_law_at_density_ratio_1_to_3():
+    """The paper's 1:3 case (alpha = (4/9, 0.8), m_B / m_A = (1 - alpha_A) /
+    (1 - alpha_B) = 25/9): droplets of the light species A in B.  The general
+    mixture pressure jumps across the interface as gamma / r with one gamma
+    for every radius (Laplace's law, Numerical Results section), and the mass
+    densities of the two bulks differ by a factor of about 2.5-3."""
+    import math
+    G, alpha, mass = 1.4, (4.0 / 9.0, 0.8), (1.0, 25.0 / 9.0)
+    inv_r, dp, ratio = [], [], []
+    for R in (9, 12, 16, 20):
+        geom = W.periodic_box(72, 72)
+        prm = dict(W.params(G, 1.0, 1.0), alpha=alpha, mass=mass)
+        nA, nB = W.droplet_fields(geom, 36.0, 36.0, R)
+        with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f32") as lat:
+            lat.step(10000)
+            a, b = lat.densities()
+        p = oracle.pressure(a, b, G, alpha, mass)
+        a_in, a_out = a[36, 36], a[0, 0]
+        inv_r.append(1.0 / math.sqrt((a - a_out).sum() / (a_in - a_out) / math.pi))
+        dp.append(p[36, 36] - p[0, 0])
+        ratio.append(mass[1] * b[0, 0] / (mass[0] * a[36, 36]))
+    inv_r, dp = np.array(inv_r), np.array(dp)
+    A = np.vstack([inv_r, np.ones_like(inv_r)]).T
+    (gamma, c0), res, *_ = np.linalg.lstsq(A, dp, rcond=None)
+    r2 = 1 - res[0] / ((dp - dp.mean()) ** 2).sum()
+    assert gamma > 0 and r2 > 0.99
+    assert abs(c0) < 0.1 * gamma * inv_r.min()
+    assert all(2.3 < q < 3.0 for q in ratio), ratio
