@@ -502,3 +502,93 @@ def test_flat_interface_pressure_balance_with_free_alpha_and_mass():
     assert abs(pA - pB) <= 1e-8 * pA
     qA, qB = oracle.pressure(a[0, 28], b[0, 28], G), oracle.pressure(a[0, 52], b[0, 52], G)
     assert abs(qA - qB) > 0.1 * qA
+
+
+# ---- brute force on a tiny grid (Model section, Eqs. 2-11) ---------------------
+
+def _brute_force_steps(solid, nA0, nB0, G, Gw, tau, alpha, mass, steps):
+    """Two species on a 5x4 grid written out node by node from the paper's
+    printed forms, independently of the oracle's loops: push streaming with
+    half-way bounce-back, the force of Eqs. 9-10 as a sum over the 8
+    neighbour offsets with g = G/9 at distance 1 and G/36 at sqrt(2), the
+    wall force with the same weights, U of Eq. 8, the shift of Eq. 7 and the
+    equilibrium in the paper's free-alpha polynomial form (Eqs. 3-5)."""
+    ny, nx = solid.shape
+    c = _eq6_velocities()
+    opp = [c.index((-a, -b)) for a, b in c]
+
+    def feq(n, u, a):
+        uu = u[0] * u[0] + u[1] * u[1]
+        out = [a * n - 2.0 / 3.0 * n * uu]
+        for i in range(1, 9):
+            cu = c[i][0] * u[0] + c[i][1] * u[1]
+            if i <= 4:
+                out.append((1 - a) * n / 5 + n * cu / 3 + n * cu * cu / 2 - n * uu / 6)
+            else:
+                out.append((1 - a) * n / 20 + n * cu / 12 + n * cu * cu / 8 - n * uu / 24)
+        return out
+
+    F = np.zeros((2, 9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            if not solid[y, x]:
+                for k, n0 in enumerate((nA0[y, x], nB0[y, x])):
+                    F[k, :, y, x] = feq(n0, (0.0, 0.0), alpha[k])
+    for _ in range(steps):
+        ft = np.zeros_like(F)
+        for y in range(ny):
+            for x in range(nx):
+                if solid[y, x]:
+                    continue
+                for i in range(9):
+                    xd, yd = (x + c[i][0]) % nx, (y + c[i][1]) % ny
+                    if solid[yd, xd]:
+                        ft[:, opp[i], y, x] = F[:, i, y, x]     # reflected back to the same node
+                    else:
+                        ft[:, i, yd, xd] = F[:, i, y, x]
+        n = ft.sum(axis=1)                                      # [2, ny, nx], 0 on solids
+        new = np.zeros_like(F)
+        for y in range(ny):
+            for x in range(nx):
+                if solid[y, x]:
+                    continue
+                force = [[0.0, 0.0], [0.0, 0.0]]
+                for dx in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        if dx == 0 and dy == 0:
+                            continue
+                        g = G / 9.0 if abs(dx) + abs(dy) == 1 else G / 36.0
+                        xn, yn = (x + dx) % nx, (y + dy) % ny
+                        for k in range(2):
+                            for d, e in ((0, dx), (1, dy)):
+                                force[k][d] -= n[k, y, x] * g * n[1 - k, yn, xn] * e
+                                if solid[yn, xn]:                  # wall force, Eq. 11
+                                    gw = Gw[k] / 9.0 if abs(dx) + abs(dy) == 1 else Gw[k] / 36.0
+                                    force[k][d] -= n[k, y, x] * gw * e
+                j = [[sum(ft[k, i, y, x] * c[i][d] for i in range(9)) for d in range(2)] for k in range(2)]
+                den = sum(mass[k] * n[k, y, x] / tau[k] for k in range(2))
+                U = [sum(mass[k] * j[k][d] / tau[k] for k in range(2)) / den for d in range(2)]
+                for k in range(2):
+                    rho = mass[k] * n[k, y, x]
+                    u = [U[d] + tau[k] * force[k][d] / rho for d in range(2)]
+                    fe = feq(n[k, y, x], u, alpha[k])
+                    for i in range(9):
+                        new[k, i, y, x] = ft[k, i, y, x] - (ft[k, i, y, x] - fe[i]) / tau[k]
+        F = new
+    return F
+
+
+@pytest.mark.parametrize("alpha,mass", [((4.0 / 9.0, 4.0 / 9.0), (1.0, 1.0)), ((0.3, 0.7), (1.0, 2.5))])
+def test_two_steps_on_a_5x4_grid_equal_brute_force(alpha, mass):
+    """Brute force on a tiny grid with a plate segment (bounce-back, wall force
+    and plate ends), unequal tau and wall couplings of both signs."""
+    geom = W.capillary_geometry(5, 4, 1, 4, 0, -1)
+    solid = W.solid_mask(geom).astype(bool)
+    nA, nB = W.random_fields(geom, 11, 0.3, 1.3)
+    G, Gw, tau = 1.1, (-0.3, 0.2), (1.0, 0.8)
+    prm = dict(W.params(G, tau[0], tau[1], Gw[0], Gw[1]), alpha=alpha, mass=mass)
+    o = oracle.OracleLattice(geom, prm, nA, nB)
+    o.step(2)
+    want = _brute_force_steps(solid, nA, nB, G, Gw, tau, alpha, mass, 2)
+    got = o.populations()
+    assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
