@@ -54,6 +54,11 @@ PROFILES = {
     (6, (128, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
     (6, (64, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
     (9, (64, 8), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
+    (9, (64, 4), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 12), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x12_f32_capillary_8192x160.txt"),
+    (9, (64, 16), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x16_f32_capillary_8192x160.txt"),
+    (6, (256, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_tile256x4_f32_capillary_8192x160.txt"),
+    (8, (32, 6), None): os.path.join(ROOT, "profiles", "k_step_tile_tile32x6_f32_capillary_8192x160.txt"),
     (9, (64, 8), SPECIES_1_3): os.path.join(ROOT, "profiles",
                                             "k_step_bidir_species_tile64x8_f32_capillary_8192x160.txt"),
 }

@@ -394,36 +394,56 @@ int autotune(lbm_t* h, int64_t* n) {
     for (int W : {32, 64})
         for (int R : {6, 14})
             if (schedule_ok(h, W, R, 8, 4)) cands.push_back({W, R, 8, 4});
-    const int per = 6;
-    if (*n < (int64_t)cands.size() * (per + 1)) return LBM_OK;  // too short to tune now
+    // pass 1: every candidate for `per` steps; pass 2: the kFinal fastest
+    // again for 2 per steps each (candidates within a few per cent of each
+    // other are told apart by the longer timing, not by the noise of pass 1)
+    const int per = 6, kFinal = 3;
+    const int64_t need = (int64_t)cands.size() * (per + 1) + (int64_t)kFinal * (2 * per + 1);
+    if (*n < need) return LBM_OK;  // too short to tune now
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    float best = 1e30f;
-    Cand bw = {h->tile_w, h->tile_h, h->kvar, h->depth};
     const int saved_chunk = h->opt.graph_chunk;
     h->opt.graph_chunk = -1;  // direct launches while timing
     int rc = LBM_OK;
-    for (const Cand& c : cands) {
+    // time candidate c over `steps` steps (after one untimed step); ms < 0 on error
+    auto time_cand = [&](const Cand& c, int steps, float& ms) {
+        ms = -1.f;
         h->kvar = c.kvar;
         h->depth = c.depth;
-        if ((rc = upload_tiles(h, c.W, c.R))) break;
-        if ((rc = advance(h, 1))) break;
+        if ((rc = upload_tiles(h, c.W, c.R))) return;
+        if ((rc = advance(h, 1))) return;
         cudaError_t e = cudaEventRecord(e0, h->stream);
-        if (e == cudaSuccess && (rc = advance(h, per))) break;
+        if (e == cudaSuccess && (rc = advance(h, steps))) return;
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
         if (e != cudaSuccess) {
             rc = cuda_fail(h, e);
-            break;
+            return;
         }
-        if (ms < best) {
-            best = ms;
-            bw = c;
+        ms = t / steps;
+        *n -= steps + 1;
+    };
+    std::vector<std::pair<float, int>> pass1;
+    for (int i = 0; i < (int)cands.size() && !rc; ++i) {
+        float ms = 0.f;
+        time_cand(cands[i], per, ms);
+        if (!rc) pass1.push_back({ms, i});
+    }
+    Cand bw = {h->tile_w, h->tile_h, h->kvar, h->depth};
+    if (!rc) {
+        std::sort(pass1.begin(), pass1.end());
+        float best = 1e30f;
+        for (int j = 0; j < kFinal && j < (int)pass1.size() && !rc; ++j) {
+            float ms = 0.f;
+            time_cand(cands[pass1[j].second], 2 * per, ms);
+            if (!rc && ms < best) {
+                best = ms;
+                bw = cands[pass1[j].second];
+            }
         }
-        *n -= per + 1;
     }
     h->opt.graph_chunk = saved_chunk;
     cudaEventDestroy(e0);
