@@ -205,3 +205,51 @@ def test_laplace_law_at_density_ratio_1_to_3():
     assert gamma > 0 and r2 > 0.99
     assert abs(c0) < 0.1 * gamma * inv_r.min()
     assert all(2.3 < q < 3.0 for q in ratio), ratio
+
+
+def test_full_size_capillary_8192x160_density_ratio_matches_oracle():
+    """The benchmark workload with the 1:3 species, in the launch
+    configuration the bench times (autotuned schedule): FP64 bit-equal to
+    the oracle after 3 steps; FP32 within 1e-5 of the density scale."""
+    c = W.config_capillary_8192x160(tau_B=1.0)
+    prm = dict(c["params"], alpha=(4.0 / 9.0, 0.8), mass=(1.0, 25.0 / 9.0))
+    nA, nB = W.initial_fields(c)
+    ref = oracle.OracleLattice(c["geom"], prm, nA, nB)
+    ref.step(3)
+    fluid = ref.solid() == 0
+    rA, rB = ref.densities()
+    run = dict(geom=c["geom"], params=prm, init=c["init"])
+    with Lattice(run, precision="f64") as lat:
+        lat.step(3)
+        assert np.array_equal(lat.populations(), ref.populations())
+    for kern, tile in ((None, (128, 4)), ((9, 4), (64, 8)), ((6, 4), (64, 4)), ((2, 4), (128, 16))):
+        with Lattice(run, precision="f32", tile=tile, kernel=kern) as lat:
+            lat.step(3)
+            gA, gB = lat.densities()
+        for g, r in ((gA, rA), (gB, rB)):
+            assert np.max(np.abs(g - r)[fluid]) / np.max(np.abs(r)) <= 1e-5
+
+
+@pytest.mark.parametrize("alpha,mass", [((0.0, 0.95), (0.5, 3.0)), ((0.99, 0.0), (4.0, 0.25))])
+def test_extreme_alpha_and_mass_match_oracle(alpha, mass):
+    """The ends of the admitted range: no rest population (alpha = 0), almost
+    all of it at rest (0.95, 0.99), masses a factor 16 apart."""
+    geom = W.periodic_box(33, 9)
+    prm = dict(W.params(0.6, 1.0, 0.7), alpha=alpha, mass=mass)
+    nA, nB = W.random_fields(geom, 21, 0.4, 1.0)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(25)
+    for kern, tile in ((None, (128, 4)), ((9, 4), (64, 8)), ((0, 4), (64, 3))):
+        with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64", tile=tile,
+                     kernel=kern) as lat:
+            lat.step(25)
+            assert np.array_equal(lat.populations(), ref.populations()), kern
+
+
+def test_alpha_and_mass_out_of_range_are_rejected():
+    from paper_0807_0602_gb300 import _lib as L
+    geom, prm, nA, nB = _capillary()
+    for bad in (dict(alpha=(1.0, 0.5)), dict(alpha=(-0.1, 0.5)), dict(mass=(0.0, 1.0)), dict(mass=(1.0, -2.0))):
+        with pytest.raises(L.LbmError) as e:
+            Lattice(dict(geom=geom, params=dict(prm, **bad), init=("fields", nA, nB)), precision="f32")
+        assert e.value.code == L.LBM_EINVAL
