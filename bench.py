@@ -250,7 +250,10 @@ def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
     and FP32 against FP64 on the first `batch_runs` runs of the uneven
     ensemble.  Densities: max |n - n_64| over the max of |n_64| (per species,
     worst of the two); fronts: max |z - z_64| in lattice units (bulk and both
-    precursors); mass: relative difference."""
+    precursors); mass: relative difference; prefactors: the Washburn slope of
+    z_bulk^2 against t and the square-root-law prefactors of z_bulk and of the
+    mean precursor front against t^(1/2), least-squares fits over the logged
+    z(t) for t >= steps/4, relative difference (worst run)."""
     import numpy as np
     import workloads as W
     from paper_0807_0602_gb300.lbm import Lattice
@@ -260,14 +263,25 @@ def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
         from paper_0807_0602_gb300._lib import LbmError
         out = []
         for run in runs:
-            with Lattice(run, precision=precision) as lat:
+            with Lattice(run, precision=precision, log_every=50, log_capacity=steps // 50 + 1) as lat:
                 lat.step(steps)
                 try:
-                    out.append((*lat.densities(), lat.interface(), lat.mass()))
+                    out.append((*lat.densities(), lat.interface(), lat.mass(), lat.log()))
                 except LbmError:
                     nan = np.full((run["geom"]["ny"], run["geom"]["nx"]), np.nan)
-                    out.append((nan, nan, np.full(3, np.nan), np.full(2, np.nan)))
+                    out.append((nan, nan, np.full(3, np.nan), np.full(2, np.nan), np.full((1, 6), np.nan)))
         return out
+
+    def prefactors(log):
+        t, zb, zp = log[:, 0], log[:, 1], 0.5 * (log[:, 2] + log[:, 3])
+        keep = t >= steps / 4
+        t, zb, zp = t[keep], zb[keep], zp[keep]
+        if len(t) < 3 or not (np.all(np.isfinite(zb)) and np.all(np.isfinite(zp))):
+            return (float("nan"),) * 3
+        A = np.vstack([t, np.ones_like(t)]).T
+        wash = np.linalg.lstsq(A, zb * zb, rcond=None)[0][0]
+        A = np.vstack([np.sqrt(t), np.ones_like(t)]).T
+        return wash, np.linalg.lstsq(A, zb, rcond=None)[0][0], np.linalg.lstsq(A, zp, rcond=None)[0][0]
 
     def compare(ref, got):
         # runs whose FP64 state stayed finite (the uneven ensemble samples parameters
@@ -278,7 +292,12 @@ def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
                  for r, g in pairs for k in (0, 1))
         dz = max(float(np.nanmax(np.abs(np.asarray(g[2]) - np.asarray(r[2])))) for r, g in pairs)
         dm = max(float(np.max(np.abs(g[3] - r[3]) / r[3])) for r, g in pairs)
-        return {"density_err_scale_rel": dn, "front_err_lu": dz, "mass_rel": dm, "finite_runs": len(ok)}
+        pf = [(prefactors(r[4]), prefactors(g[4])) for r, g in pairs]
+        rel = lambda a, b: float(abs(a - b) / max(abs(a), 1e-300))
+        return {"density_err_scale_rel": dn, "front_err_lu": dz, "mass_rel": dm, "finite_runs": len(ok),
+                "washburn_prefactor_rel": max(rel(a[0], b[0]) for a, b in pf),
+                "sqrt_prefactor_bulk_rel": max(rel(a[1], b[1]) for a, b in pf),
+                "sqrt_prefactor_precursor_rel": max(rel(a[2], b[2]) for a, b in pf)}
 
     c = workload()
     run = [dict(geom=c["geom"], params=c["params"], init=c["init"])]
