@@ -248,7 +248,8 @@ def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
     """The error at which the throughput is quoted: FP32 and FP16-shifted
     storage against the FP64 GPU build after `steps` steps of the workload,
     and FP32 against FP64 on the first `batch_runs` runs of the uneven
-    ensemble.  Densities: max |n - n_64| over the max of |n_64| (per species,
+    ensemble (FP16S offsets from workloads.fp16_shift: each species' density
+    in the majority phase).  Densities: max |n - n_64| over the max of |n_64| (per species,
     worst of the two); fronts: max |z - z_64| in lattice units (bulk and both
     precursors); mass: relative difference; prefactors: the Washburn slope of
     z_bulk^2 against t and the square-root-law prefactors of z_bulk and of the
@@ -263,7 +264,9 @@ def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
         from paper_0807_0602_gb300._lib import LbmError
         out = []
         for run in runs:
-            with Lattice(run, precision=precision, log_every=50, log_capacity=steps // 50 + 1) as lat:
+            shift = W.fp16_shift(run) if precision == "f16s" else (0.0, 0.0)
+            with Lattice(run, precision=precision, log_every=50, log_capacity=steps // 50 + 1,
+                         rho_ref=shift) as lat:
                 lat.step(steps)
                 try:
                     out.append((*lat.densities(), lat.interface(), lat.mass(), lat.log()))

@@ -167,6 +167,15 @@ def batch_sessile_droplets(n: int = 1024, seed: int = 4, nx: int = 256, ny: int 
     return runs
 
 
+def fp16_shift(run: dict):
+    """FP16-shifted storage offset rho_ref per species: the species' density in
+    the phase that fills most of the run's fluid nodes (the median of its
+    initial field), so that most stored values are small."""
+    nA, nB = initial_fields(run)
+    fluid = solid_mask(run["geom"]) == 0
+    return float(np.median(nA[fluid])), float(np.median(nB[fluid]))
+
+
 def initial_fields(run: dict):
     """Initial (nA, nB) of a run dict built by this module."""
     kind = run["init"][0]
