@@ -56,6 +56,8 @@ extern "C" {
 #define LBM_ETIMEOUT 5    /* a bounded device wait gave up */
 #define LBM_ESTATE 6      /* the call needs state the handle does not have (no log, t = 0, ...) */
 #define LBM_EIO 7         /* checkpoint file could not be written or read, or is malformed */
+#define LBM_EBOUNDS 8     /* checked builds (-DLBM_CHECKED) only: a kernel found a tile or row outside
+                             its run's buffers and skipped every access of it */
 
 /* ---- storage precision of the populations ------------------------------- */
 #define LBM_F64 0   /* FP64 populations and FP64 arithmetic */

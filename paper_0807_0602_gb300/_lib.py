@@ -10,13 +10,13 @@ import ctypes
 import os
 import threading
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 c_int32, c_int64, c_double, c_void_p, c_size_t = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
                                                   ctypes.c_void_p, ctypes.c_size_t)
 P = ctypes.POINTER
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = range(8)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO, LBM_EBOUNDS = range(9)
 LBM_F64, LBM_F32, LBM_F16S = 0, 1, 2
 LBM_INIT_SLAB, LBM_INIT_DROPLET, LBM_INIT_FIELDS = 0, 1, 2
 
@@ -99,15 +99,18 @@ class LbmError(RuntimeError):
 
 
 def load():
-    """Loads the in-tree library; raises if it has not been built."""
+    """Loads the in-tree library; raises if it has not been built.  With the
+    environment variable LBM_CHECKED=1 the process loads the checked build
+    (build(checked=True)) instead."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB):
+            path = LIB_CHECKED if os.environ.get("LBM_CHECKED") == "1" else LIB
+            if not os.path.exists(path):
                 raise RuntimeError(
-                    f"CUDA library {LIB} is missing: build it with paper_0807_0602_gb300.build.build() "
+                    f"CUDA library {path} is missing: build it with paper_0807_0602_gb300.build.build() "
                     "(there is no CPU fallback)")
-            lib = ctypes.CDLL(LIB)
+            lib = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)
                 fn.restype = res

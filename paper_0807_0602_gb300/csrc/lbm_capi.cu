@@ -7,6 +7,8 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_device.h"
 
@@ -78,7 +80,8 @@ namespace {
 
 const char* kErr[] = {"ok", "invalid argument", "out of device memory", "CUDA error",
                       "non-finite mass (the run diverged)", "device wait timed out",
-                      "state not available", "checkpoint I/O error"};
+                      "state not available", "checkpoint I/O error",
+                      "index outside the run's buffers (checked build)"};
 
 int cuda_fail(lbm_t* h, cudaError_t e) {
     if (e == cudaSuccess) return LBM_OK;
@@ -340,6 +343,15 @@ int get_graph(lbm_t* h, int parity, int steps, int with_log, cudaGraphExec_t* ou
     return LBM_OK;
 }
 
+// NVTX range over a scope (header-only NVTX: a no-op unless a profiler is
+// attached), so that traces show step chunks, logs and tuning by name.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Advances by n steps without autotuning.
 int advance(lbm_t* h, int64_t n) {
     const int le = h->opt.log_every;
@@ -351,6 +363,7 @@ int advance(lbm_t* h, int64_t n) {
         if (le > 0) m = std::min<int64_t>(n, le - (h->t % le));
         else m = std::min<int64_t>(n, chunk);
         if (graphs && m == chunk && (le == 0 || h->t % le == 0)) {
+            NvtxRange range("lbm graph chunk");
             cudaGraphExec_t ex;
             int rc = get_graph(h, (int)(h->t & 1), chunk, le > 0, &ex);
             if (rc) return rc;
@@ -358,6 +371,7 @@ int advance(lbm_t* h, int64_t n) {
             h->t += m;
             if (le > 0) h->nlog += 1;
         } else {
+            NvtxRange range("lbm steps");
             for (int64_t j = 0; j < m; ++j) {
                 CK(h, issue_step(h, (int)(h->t & 1), h->stream));
                 h->t += 1;
@@ -464,7 +478,8 @@ int read_err(lbm_t* h) {
     uint32_t e = 0;
     CK(h, cudaMemcpyAsync(&e, h->d_err, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (e & sc::ERR_NONFINITE) h->sticky = LBM_ENONFINITE;
+    if (e & sc::ERR_BOUNDS) h->sticky = LBM_EBOUNDS;
+    else if (e & sc::ERR_NONFINITE) h->sticky = LBM_ENONFINITE;
     else if (e & sc::ERR_TIMEOUT) h->sticky = LBM_ETIMEOUT;
     return h->sticky;
 }
@@ -621,6 +636,7 @@ int create_impl(int n, const lbm_geometry* g, const double* G_AB, const double* 
             h->track_cap = std::max(h->track_cap, rd.cap_x1 - rd.cap_x0);
     h->d_rows = static_cast<int2*>(dalloc(h, h->rows.size() * sizeof(int2)));
     h->d_runs = static_cast<RunDesc*>(dalloc(h, (size_t)n * sizeof(RunDesc)));
+    for (RunDesc& rd : h->runs) rd.err = h->d_err;
     if (!h->d_logcount || !h->d_err || !h->d_partials || !h->d_mass || !h->d_zout || !h->d_first || !h->d_rows ||
         !h->d_runs)
         return fail(LBM_ENOMEM);
@@ -722,7 +738,9 @@ int lbm_create_batch(int n, const lbm_geometry* g, const double* G_AB, const dou
 int lbm_step(lbm_t* h, int64_t n_steps) {
     if (!h || n_steps < 0) return LBM_EINVAL;
     if (h->sticky) return h->sticky;
+    NvtxRange range("lbm_step");
     if (!h->tuned) {
+        NvtxRange tune("lbm autotune");
         int rc = autotune(h, &n_steps);
         if (rc) return rc;
     }
@@ -1076,7 +1094,7 @@ int lbm_status(lbm_t* h) {
 }
 
 const char* lbm_error_string(int code) {
-    if (code < 0 || code > LBM_EIO) return "unknown status";
+    if (code < 0 || code > LBM_EBOUNDS) return "unknown status";
     return kErr[code];
 }
 

@@ -45,6 +45,7 @@ struct RunDesc {
     const double* init_nA;    // device [ny][nx] (LBM_INIT_FIELDS)
     const double* init_nB;
     double* log;              // device ring [cap][6] of this run, or nullptr
+    uint32_t* err;            // the handle's device error word (ERR_* bits)
 };
 
 // Fills rd.c32 from the FP64 fields (round to nearest, as a device conversion
@@ -100,7 +101,7 @@ struct LogCtl {
     int log_every;
 };
 
-enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
+enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u, ERR_BOUNDS = 4u };   // ERR_BOUNDS: checked builds
 
 // Step kernels (one pass of Eq. 2 over every tile) and the moments pass.
 // GEN: the runs have some alpha_k != 4/9 or m_k != 1.

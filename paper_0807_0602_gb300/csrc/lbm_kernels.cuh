@@ -480,6 +480,24 @@ struct StripCols {
     }
 };
 
+// Checked builds (-DLBM_CHECKED): before touching memory, every step kernel
+// checks its tile against its run and the run's layout (the invariants all
+// row and column indices of the march derive from).  On a violation it sets
+// ERR_BOUNDS in the handle's error word and the whole CTA returns without an
+// access.  Other builds compile the check away.
+__device__ __forceinline__ bool step_tile_ok(const Tile& tl, const RunDesc& rd) {
+#ifdef LBM_CHECKED
+    const bool ok = tl.x0 >= 0 && tl.x0 < rd.nx && tl.y0 >= 0 && tl.y0 < tl.y1 && tl.y1 <= rd.ny &&
+                    rd.nx >= 1 && rd.pitch >= rd.nx + 2 * LBM_COL0 && rd.plane == (long long)rd.ny * rd.pitch;
+    if (!ok && threadIdx.x == 0 && rd.err) atomicOr(rd.err, ERR_BOUNDS);
+    return ok;
+#else
+    (void)tl;
+    (void)rd;
+    return true;
+#endif
+}
+
 // MODE 0: one time step (read buf[parity], write buf[parity ^ 1]).
 // MODE 1: moments of the step from buf[parity] (whole-fluid velocity), no write.
 // Pulled populations travel through registers (plain loads).
@@ -521,6 +539,7 @@ __global__ void __launch_bounds__(W, (kMinBlocks<S, W>)) k_step(const RunDesc* _
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const long long plane = rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -744,6 +763,7 @@ __global__ void __launch_bounds__(2 * W, (kSplitMinBlocks<S, W>)) k_step_split(c
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const long long plane = rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -821,6 +841,7 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const long long plane = rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -902,6 +923,7 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -1035,6 +1057,7 @@ __global__ void __launch_bounds__(W, (kPairMinBlocks<S, W>)) k_step_pair(const R
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -1210,6 +1233,7 @@ __global__ void __launch_bounds__(W * TY, (kTileMinBlocks<S, W, TY>)) k_step_til
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
@@ -1303,6 +1327,7 @@ __global__ void __launch_bounds__(W, (kPipeMinBlocks<S, W>)) k_step_pf(const Run
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -1415,6 +1440,7 @@ __global__ void __launch_bounds__(W) k_step_async(const RunDesc* __restrict__ ru
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const long long plane = rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -1624,6 +1650,7 @@ __global__ void __launch_bounds__(W) k_step_tma(const RunDesc* __restrict__ runs
 
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
+    if (!step_tile_ok(tl, rd)) return;
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
@@ -2064,6 +2091,12 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_rows(const RunDesc* __res
                                                             double* __restrict__ partials) {
     const int2 ry = rows[blockIdx.x];
     const RunDesc& rd = runs[ry.x];
+#ifdef LBM_CHECKED
+    if (ry.y < 0 || ry.y >= rd.ny) {
+        if (threadIdx.x == 0 && rd.err) atomicOr(rd.err, ERR_BOUNDS);
+        return;
+    }
+#endif
     mass_row_sum<S>(rd, static_cast<const S*>(rd.buf[parity]), ry.y, blockIdx.y, kMassChunks,
                     partials + 2 * ((long long)blockIdx.x * kMassChunks + blockIdx.y));
 }

@@ -131,7 +131,7 @@ def test_null_handles_and_status_strings(lib):
     assert lib.lbm_step(None, 1) == L.LBM_EINVAL
     assert lib.lbm_time(None) == -1
     lib.lbm_destroy(None)
-    for code in range(8):
+    for code in range(9):
         assert lib.lbm_error_string(code)
     assert lib.lbm_error_string(99) == b"unknown status"
 
@@ -151,3 +151,15 @@ def test_structure_layouts_match_header():
     # 8 int32 + 5 doubles + 4 pointers + 4 doubles
     assert ctypes.sizeof(L.Options) == 8 * 4 + 5 * 8 + 4 * 8 + 4 * 8
     assert ctypes.sizeof(L.RunInfo) == 6 * 4 + 8 + 2 * 8
+
+
+def test_checked_build_compiles_and_exports_the_same_symbols(lib):
+    """The -DLBM_CHECKED variant (bounds checks in every step kernel) builds
+    and exports the same ABI as the default library."""
+    from paper_0807_0602_gb300 import build as B
+    path = B.build(checked=True)
+    checked = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(checked, n)]
+    assert not missing, missing
+    checked.lbm_error_string.restype = ctypes.c_char_p
+    assert b"checked" in checked.lbm_error_string(8)
