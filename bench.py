@@ -16,6 +16,9 @@ value     GLUPS (lattice node updates of both species per second, all nodes),
 e2e       the same metric for the whole job through the C ABI with host
           buffers: initial fields uploaded from pinned host memory, the steps,
           the log and the final densities copied back, inside the timed region.
+          The steps run back to back (CUDA graphs, no flush), as in a user's
+          loop: part of a step's input is still in L2 from the step before, so
+          e2e can exceed value.
 roofline  the step kernel: algorithmic bytes (18 populations read + written
           per fluid node, storage precision) / its average launch time,
           against the measured HBM copy bandwidth.
