@@ -5,7 +5,10 @@
  * potential lattice Boltzmann model of S. Chibbaro, "Capillary filling with
  * pseudo-potential binary Lattice-Boltzmann model":
  *   - per-component BGK equation, Eq. 2 (eq:lbe), Delta t = 1;
- *   - D2Q9 equilibrium, Eqs. 3-5 with alpha_k = 4/9 and m_k = 1;
+ *   - D2Q9 equilibrium, Eqs. 3-5, with rest fraction alpha_k and molecular
+ *     mass m_k per species (rho_k = m_k n_k); the defaults alpha_k = 4/9,
+ *     m_k = 1 give the standard D2Q9 weights (lbm_options.alpha and
+ *     molecular_mass);
  *   - equilibrium-velocity shift rho_k u_k^eq = rho_k U + tau_k F_k, Eq. 7,
  *     with the common velocity U of Eq. 8 (sum over the species);
  *   - bulk force of Eq. 9 with Psi_k = n_k and the coupling written with the
@@ -27,8 +30,9 @@
  *
  * Conventions for every call:
  *   - Return value: LBM_OK (0) or a positive LBM_E* code; no exception
- *     crosses the ABI.  Errors raised by kernels (non-finite mass, timeout)
- *     are sticky and reported by the next synchronising call.
+ *     crosses the ABI.  Errors raised by kernels (non-finite mass, timeout,
+ *     and in checked builds an index outside the buffers) are sticky and
+ *     reported by the next synchronising call.
  *   - All work is issued on the stream given in lbm_options at creation
  *     (NULL = the legacy default stream) and is asynchronous unless the
  *     call says it synchronises.
