@@ -217,6 +217,20 @@ def test_mass_conserved_with_plates():
     assert np.all(np.abs(o.mass() - M0) <= 1e-13 * M0)
 
 
+@pytest.mark.slow
+def test_mass_conserved_over_1e4_steps_with_plates_and_free_alpha():
+    """Per-species mass to 1e-12 relative after 10^4 steps (BGK conserves
+    sum_i f, bounce-back moves populations without loss), for the standard
+    and the density-ratio model."""
+    geom = W.capillary_geometry(24, 10, 4, 20, 0, 9)
+    for extra in ({}, dict(alpha=(4.0 / 9.0, 0.8), mass=(1.0, 25.0 / 9.0))):
+        prm = dict(W.params(1.0, 1.0, 1.0, -0.2, 0.0), **extra)
+        o = _lattice(geom, prm, W.slab_fields(geom, 0, 10))
+        M0 = o.mass()
+        o.step(10000)
+        assert np.all(np.abs(o.mass() - M0) <= 1e-12 * M0)
+
+
 def test_total_momentum_conserved_in_periodic_box_with_unequal_tau():
     # sum_k (n_k U - j_k)/tau_k = 0 by Eq. 8, and the pair forces of Eq. 9
     # cancel pairwise; a wrong weighting of U or an asymmetric force breaks it
