@@ -2,9 +2,12 @@
 // with pseudo-potential binary Lattice-Boltzmann model", Model section,
 // Eqs. 2-11; Numerical Results section for geometry, bounce-back and fronts).
 //
-// Included by exactly two translation units: kernels_f64.cu (FP64, built with
+// Included (through lbm_launch.cuh) by one translation unit per storage type
+// and species model: kernels_f64.cu / kernels_gen_f64.cu (FP64, built with
 // --fmad=false so that every product and sum is rounded separately, in the
-// canonical order below) and kernels_f32.cu (FP32 and FP16-shifted storage).
+// canonical order below), kernels_f32.cu / kernels_gen_f32.cu (FP32) and
+// kernels_f16.cu / kernels_gen_f16.cu (FP16-shifted storage); the _gen units
+// hold the step kernels of the free-alpha, m_k != 1 species model.
 //
 // Canonical per-node order (both precisions; FP64 reproduces it bit for bit):
 //   1. pull: ft_i(x) = F_i(x - c_i), or F_opp(i)(x) when x - c_i is solid

@@ -1,5 +1,6 @@
-// Launchers of the kernels in lbm_kernels.cuh; instantiated per storage type
-// by kernels_f64.cu and kernels_f32.cu.
+// Launchers of the kernels in lbm_kernels.cuh; Launch<S> is instantiated per
+// storage type by kernels_f64.cu, kernels_f32.cu and kernels_f16.cu, and
+// Step<S, GEN> by those and by the kernels_gen_*.cu units (GEN = true).
 #pragma once
 
 #include <atomic>
