@@ -249,8 +249,10 @@ int lbm_get_log(lbm_t* h, int run, double* rec, int capacity, int* n_rec);
 /* Per-species mass M_k = sum over fluid nodes and i of f_i^k, summed in
  * FP64 in a fixed order (deterministic).  The collision and the streaming
  * with bounce-back conserve it (Numerical Results section: periodic sides
- * for total mass conservation).  Host output M[2]; synchronises.  Sets and
- * returns LBM_ENONFINITE if a sum is NaN or infinite. */
+ * for total mass conservation).  With molecular masses m_k != 1 this is the
+ * number of particles of species k; its mass is m_k M_k.  Host output M[2];
+ * synchronises.  Sets and returns LBM_ENONFINITE if a sum is NaN or
+ * infinite. */
 int lbm_mass(lbm_t* h, int run, double M[2]);
 
 /* Copies the populations of time t of run `run` (storage precision, layout
