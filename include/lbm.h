@@ -84,7 +84,8 @@ typedef struct lbm_s lbm_t;
  *             plates for the force, the bounce-back and the tracking rows
  *             (the tracking rows still follow y_bot/y_top).  Copied at create.
  * init_*      initial layout; the state starts at rest in equilibrium
- *             (f_i = w_i n_k), solid nodes carry no fluid.  Liquid nodes get
+ *             (f_i = A_i(alpha_k) n_k, = w_i n_k at alpha_k = 4/9), solid
+ *             nodes carry no fluid.  Liquid nodes get
  *             (n_A, n_B) = (rho_major, rho_minor), gas nodes the reverse.
  *             init_nA / init_nB (LBM_INIT_FIELDS) are host [ny][nx] arrays,
  *             copied at create. */
@@ -112,9 +113,12 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  * log_every     record (t, z_bulk, z_prec_bottom, z_prec_top, M_A, M_B) every
  *               log_every steps, including t = 0; 0 = no log.
  * log_capacity  records kept per run (a ring: the newest log_capacity).
- * autotune      1 = time the candidate tilings during the first steps of
- *               lbm_step and keep the fastest.  Tilings change only the
- *               schedule: results are bit-identical for every tiling.
+ * autotune      1 = time the candidate tilings during the first lbm_step
+ *               call long enough for them (every candidate for 6 steps,
+ *               the 3 fastest again for 12; about 570 steps on a large
+ *               grid) and keep the fastest.  These are real steps: tilings
+ *               change only the schedule, and results are bit-identical for
+ *               every tiling.
  * tile_w        CTA width (64, 128 or 256 threads; 0 = default 128);
  * tile_h        rows marched per CTA (0 = default 4, clamped to ny).
  *               The step kernel starts as LBM_KERNEL_SMEM where it takes the
