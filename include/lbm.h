@@ -183,7 +183,8 @@ typedef struct lbm_run_info {
     void* base[2];
 } lbm_run_info;
 
-/* Fills opt with the defaults documented above (FP32, no log, tile 128x16). */
+/* Fills opt with the defaults documented above (FP32, no log, tile 128x4,
+ * alpha 4/9, molecular mass 1). */
 void lbm_default_options(lbm_options* opt);
 
 /* Creates one run (Model section: Eqs. 2-11 with the given couplings).
