@@ -249,6 +249,48 @@ def measure_batched(world: int, rank: int, stream, precision: str = "f32", steps
             "note": "inputs 24 GB >> L2, no flush needed; all nodes counted"}
 
 
+def measure_density_ratio(stream, dev, precision: str, steps: int = 1000):
+    """The workload with the paper's 1:3 species (alpha = (4/9, 0.8),
+    m = (1, 25/9)): autotuned, then `steps` steps timed one by one with CUDA
+    events after the same L2 flush as the headline, log every 50 steps."""
+    import numpy as np
+    import torch
+    from paper_0807_0602_gb300.lbm import Lattice
+    c = workload()
+    g = c["geom"]
+    prm = dict(c["params"], alpha=SPECIES_1_3[:2], mass=SPECIES_1_3[2:])
+    nodes, fluid = g["nx"] * g["ny"], g["nx"] * g["ny"] - 2 * (g["cap_x1"] - g["cap_x0"])
+    with torch.cuda.stream(stream):
+        lat = Lattice(dict(geom=g, params=prm, init=c["init"]), precision=precision, log_every=50,
+                      log_capacity=4096, autotune=True, stream=stream)
+        lat.step(650)
+        lat.sync()
+        fw = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        fr = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        acc = torch.empty((), dtype=torch.float32, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = lat.t
+        for a, b in ev:
+            fw.zero_()
+            torch.sum(fr, 0, out=acc)
+            a.record(stream)
+            lat.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        durs = [a.elapsed_time(b) for a, b in ev]
+        kern = [d for k, d in enumerate(durs) if (t0 + k + 1) % 50 != 0]
+        sched = lat.schedule
+        finite = bool(np.all(np.isfinite(lat.mass())))
+        lat.close()
+    kernel_ms = statistics.mean(kern)
+    peak, _ = peaks()
+    gbs = fluid * BYTES_PER_NODE[precision] / (kernel_ms * 1e-3) / 1e9
+    return {"value": nodes * steps / (sum(durs) * 1e-3) / 1e9, "unit": "GLUPS", "steps": steps,
+            "alpha": list(SPECIES_1_3[:2]), "mass": list(SPECIES_1_3[2:]), "kernel_ms": kernel_ms,
+            "alg_GBs": gbs, "frac": gbs / peak, "schedule": {"tile": list(sched[:2]), "kernel": KERNELS[sched[2]]},
+            "state_finite": finite}
+
+
 def measure_accuracy(steps: int = 2000, batch_runs: int = 16):
     """The error at which the throughput is quoted: FP32 and FP16-shifted
     storage against the FP64 GPU build after `steps` steps of the workload,
@@ -690,6 +732,8 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
 
     batched = None if args.no_batched else measure_batched(world, rank, stream, args.precision)
+    density_ratio = (measure_density_ratio(stream, dev, args.precision)
+                     if (rank == 0 and not args.no_batched and SPECIES is None) else None)
     surrogate = measure_surrogate() if (rank == 0 and not args.no_batched) else None
     accuracy = measure_accuracy() if (rank == 0 and not args.no_batched) else None
     if rank != 0:
@@ -722,6 +766,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched
+        if density_ratio is not None:
+            line["density_ratio"] = density_ratio
         line["surrogate"] = surrogate
         line["accuracy"] = accuracy
     if not args.no_cpu_baseline and world == 1:
