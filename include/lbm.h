@@ -128,8 +128,10 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  *               -1 = launch every step directly).
  * rho_ref       FP16S shift per species (ignored otherwise).
  * rho_bulk      base of the precursor threshold rho_bulk / 3 (0 = 2.0).
- * body          constant body acceleration added to both species' a_k
- *               (drives the Poiseuille check; 0 for capillary filling).
+ * body          constant body force per particle, added to F_k / n_k of
+ *               both species (an acceleration when m_k = 1; species k then
+ *               accelerates by body / m_k).  Drives the Poiseuille check; 0
+ *               for capillary filling.
  * alloc/free    optional device allocator; NULL = cudaMallocAsync on stream.
  * stream        cudaStream_t of all work; NULL = legacy default stream.
  * alpha         rest fraction alpha_k of each species' equilibrium (Model

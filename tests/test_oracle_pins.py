@@ -606,3 +606,23 @@ def test_two_steps_on_a_5x4_grid_equal_brute_force(alpha, mass):
     want = _brute_force_steps(solid, nA, nB, G, Gw, tau, alpha, mass, 2)
     got = o.populations()
     assert np.max(np.abs(got - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_mass_weighted_velocity_of_a_uniform_mixture_under_a_body_force():
+    """Closed form of the whole-fluid velocity with masses (Model section,
+    below Eq. 12, rho u = sum_k m_k j_k + (1/2) sum_k F_k, rho = sum_k m_k
+    n_k): a uniform mixture at rest with a body force g per particle.  After
+    one step the streamed state is still at rest, so u = g sum n / (2 rho).
+    The first collision leaves species k with momentum n_k g / m_k (the
+    shift of Eq. 7 is tau_k F_k / rho_k), so after two steps
+    u = 3 g sum n / (2 rho)."""
+    geom = W.periodic_box(5, 4)
+    n0, m, g = (0.9, 0.4), (1.0, 2.5), (1e-3, -2e-3)
+    prm = dict(W.params(0.0, 0.9, 1.2, body=g), alpha=(4.0 / 9.0, 0.7), mass=m)
+    o = _lattice(geom, prm, (np.full((4, 5), n0[0]), np.full((4, 5), n0[1])))
+    rho = m[0] * n0[0] + m[1] * n0[1]
+    for steps, factor in ((1, 0.5), (1, 1.5)):
+        o.step(steps)
+        ux, uy = o.velocity()
+        assert np.allclose(ux, factor * g[0] * sum(n0) / rho, rtol=1e-12, atol=0)
+        assert np.allclose(uy, factor * g[1] * sum(n0) / rho, rtol=1e-12, atol=0)
