@@ -6,9 +6,9 @@ the equilibrium-velocity shift, cross-species pseudo-potential force, wall
 force setting the contact angle, half-way bounce-back on the plates, and the
 bulk-interface and precursor-film fronts z(t); species with the standard
 D2Q9 equilibrium or with a free rest fraction alpha_k and molecular mass m_k
-(density ratios).  The step runs in hand-written
-CUDA kernels for sm_103a behind the C ABI of include/lbm.h; this package holds
-the Python binding (``Lattice``), the host-side analysis and the build step.
+(density ratios).  The step runs in hand-written CUDA kernels for sm_103a
+behind the C ABI of include/lbm.h; this package holds the Python binding
+(``Lattice``), the host-side analysis and the build step.
 """
 from .build import build as build_library  # noqa: F401
 
