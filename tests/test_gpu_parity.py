@@ -422,3 +422,36 @@ def test_solid_mask_schedules_bit_identical(prec):
             outs.append(lat.populations())
     for o in outs[1:]:
         assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
+
+
+def test_fp64_mini_capillary_1e4_steps_matches_oracle():
+    """FP64 GPU against the oracle after 10^4 steps on the 64x18 mini
+    capillary (stable parameters): bit-equal populations, equal fronts."""
+    geom = W.capillary_geometry(64, 18, 16, 48, 0, 17)
+    prm = W.params(1.0, 1.0, 1.0, -0.2, 0.0)
+    nA, nB = W.slab_fields(geom, 0, 24)
+    ref = oracle.OracleLattice(geom, prm, nA, nB)
+    ref.step(10000)
+    with Lattice(dict(geom=geom, params=prm, init=("fields", nA, nB)), precision="f64") as lat:
+        lat.step(10000)
+        F = lat.populations()
+        z = lat.interface()
+    assert np.all(np.isfinite(F))
+    assert np.array_equal(F, ref.populations())
+    assert np.max(np.abs(np.asarray(z) - np.asarray(ref.interface()))) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_repeated_runs_are_bit_identical(prec):
+    """Two handles on the same input give the same bits (fixed reduction
+    orders, order-free integer minima, no atomics on floating-point data);
+    with the log on, so that the mass sums and front scans run too."""
+    c = W.config_capillary_8192x160(tau_B=1.0)
+    run = dict(geom=c["geom"], params=dict(c["params"], G=1.0, G_Aw=-0.3), init=c["init"])
+    outs = []
+    for _ in range(2):
+        with Lattice(run, precision=prec, rho_ref=(0.04, 2.0), log_every=50, log_capacity=16) as lat:
+            lat.step(300)
+            outs.append((lat.populations(), lat.log(), lat.mass()))
+    assert np.array_equal(outs[0][0].view(np.uint8), outs[1][0].view(np.uint8))
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
