@@ -515,102 +515,6 @@ def run_profile(args):
     return 0
 
 
-SWEEP = [(128, 16, 0, 4), (64, 16, 0, 4), (128, 4, 6, 4), (128, 8, 6, 4), (64, 4, 6, 4), (128, 8, 9, 4),
-         (128, 6, 9, 4), (128, 10, 9, 4), (64, 8, 9, 4), (64, 4, 7, 4),
-         (64, 8, 7, 4), (32, 6, 8, 4), (32, 14, 8, 4), (128, 8, 2, 4), (128, 16, 2, 4), (128, 8, 1, 4),
-         (128, 4, 3, 4), (128, 16, 4, 4), (128, 16, 5, 4)]
-
-
-def run_sweep(args):
-    """Times every step-kernel variant over a few tilings on the workload
-    (CUDA events, L2 flushed as in the timed run); one JSON line each."""
-    import torch
-    from paper_0807_0602_gb300.build import build as build_lib
-    from paper_0807_0602_gb300.lbm import Lattice
-    build_lib()
-    c = workload()
-    g = c["geom"]
-    fluid_nodes = g["nx"] * g["ny"] - 2 * (g["cap_x1"] - g["cap_x0"])
-    peak, _ = peaks()
-    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    acc = torch.empty((), dtype=torch.float32, device="cuda")
-    for sched in SWEEP:
-        if args.precision == "f16s" and sched[2] == 1:
-            continue   # the cp.async kernel moves 4- or 8-byte elements only
-        with Lattice(dict(geom=g, params=c["params"], init=c["init"]), precision=args.precision, tile=sched[:2],
-                     kernel=sched[2:], graph_chunk=-1) as lat:
-            lat.step(20)
-            lat.sync()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-            for a, b in ev:
-                flush_w.zero_()
-                torch.sum(flush_r, 0, out=acc)
-                a.record()
-                lat.step(1)
-                b.record()
-            torch.cuda.synchronize()
-        us = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e3
-        gbs = fluid_nodes * BYTES_PER_NODE[args.precision] / (us * 1e-6) / 1e9
-        print(json.dumps({"schedule": list(sched), "kernel": KERNELS[sched[2]], "precision": args.precision,
-                          "us_per_step": us, "GLUPS": g["nx"] * g["ny"] / (us * 1e-6) / 1e9, "alg_GBs": gbs,
-                          "frac": gbs / peak, "steps": args.steps}), flush=True)
-    return 0
-
-
-def run_probe(args):
-    """The step's memory access pattern without its arithmetic (lbm_probe.h)
-    on the workload's grid and layout, at several resident-thread counts per
-    SM (set with unused dynamic shared memory), timed like the step (CUDA
-    events, L2 flushed before each pass); one JSON line per case."""
-    import ctypes
-    import torch
-    from paper_0807_0602_gb300 import _lib as L
-    from paper_0807_0602_gb300.build import build as build_lib
-    build_lib()
-    lib = L.load()
-    c = workload()
-    nx, ny = c["geom"]["nx"], c["geom"]["ny"]
-    pitch = (nx + 16 + 63) // 64 * 64
-    src = torch.rand(18 * ny * pitch, device="cuda")
-    dst = torch.zeros_like(src)
-    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    acc = torch.empty((), dtype=torch.float32, device="cuda")
-    peak, _ = peaks()
-    stream = torch.cuda.current_stream()
-    nodes = (nx - 2) * (ny - 2)
-    # 128-thread CTAs: resident threads per SM 2048 (no padding), 1024, 640, 512
-    occupancy = {2048: 0, 1024: 28 * 1024, 640: 45 * 1024, 512: 56 * 1024}
-    cases = [("pull", 0, 1), ("copy", 1, 1), ("march", 2, 4), ("march", 2, 8), ("march", 2, 16),
-             ("pull-blocked", 3, 1), ("copy-blocked", 4, 1)]
-    for threads, smem in occupancy.items():
-        for name, pattern, rows in cases:
-            def launch():
-                rc = lib.lbm_probe_stream(pattern, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
-                                          nx, ny, pitch, rows, 128, smem, ctypes.c_void_p(stream.cuda_stream))
-                if rc != 0:
-                    raise RuntimeError(f"lbm_probe_stream failed ({rc})")
-            for _ in range(3):
-                launch()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-            for a, b in ev:
-                flush_w.zero_()
-                torch.sum(flush_r, 0, out=acc)
-                a.record()
-                launch()
-                b.record()
-            torch.cuda.synchronize()
-            us = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e3
-            n_used = (nx - 64) * (ny - 2) if pattern >= 3 else nodes
-            gbs = n_used * 144 / (us * 1e-6) / 1e9
-            print(json.dumps({"probe": name, "rows": rows, "threads_per_sm": threads, "us": us, "alg_GBs": gbs,
-                              "frac": gbs / peak, "grid": [nx, ny], "passes": args.steps}), flush=True)
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -624,12 +528,8 @@ def main():
                     help="only step the workload this many times (for ncu captures) and exit")
     ap.add_argument("--schedule", default="128,4,6,4",
                     help="tile_w,tile_h,kernel,depth used by --profile")
-    ap.add_argument("--sweep", action="store_true",
-                    help="time every step-kernel variant on the workload (--steps steps each) and exit")
     ap.add_argument("--species", default=None,
                     help="alpha_A,alpha_B,m_A,m_B: rest fractions (Eqs. 3-5) and molecular masses of the species")
-    ap.add_argument("--probe", action="store_true",
-                    help="time the step's memory access pattern without arithmetic (--steps passes each) and exit")
     args = ap.parse_args()
     if args.species:
         global SPECIES
@@ -640,10 +540,6 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
-    if args.sweep:
-        return run_sweep(args)
-    if args.probe:
-        return run_probe(args)
     args.warmup = max(3, args.warmup)
 
     world, rank, local = dist_setup(args.gpus)
@@ -729,7 +625,11 @@ def main():
     h2d = 2 * nodes * 8
     d2h = log.nbytes + dA.nbytes + dB.nbytes
     e2e = {"value": world * nodes * args.steps / e2e_s / 1e9, "unit": "GLUPS",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "steps": args.steps,
+           "note": "host wall clock over lbm_create from pinned host fields (21 MB upload), the steps, "
+                   "the log and both densities copied back; at a few tens of steps creation and the "
+                   "copies dominate, at thousands the steps do"}
 
     batched = None if args.no_batched else measure_batched(world, rank, stream, args.precision)
     density_ratio = (measure_density_ratio(stream, dev, args.precision)

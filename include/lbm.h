@@ -325,12 +325,14 @@ int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
 
 /* Per-species FP64 mass of one population buffer, computed without
  * allocating any memory.  The paper has no counterpart: this is plumbing for
- * callers that cannot allocate device memory where they need the sums, for
- * instance code running while a CUDA graph is being captured (where
- * cudaMalloc is not permitted), a callback of a caching allocator that must
- * not re-enter it, or a process whose device memory is entirely reserved by
- * another framework's pool.  It computes what lbm_mass computes, in the same
- * order, from a caller-owned buffer instead of a handle.
+ * callers that cannot allocate device memory at the point where they need
+ * the sums, for instance a callback of a caching allocator that must not
+ * re-enter that allocator, or a process whose device memory is entirely
+ * reserved by another framework's pool (a cudaMalloc there would fail or
+ * fragment the pool).  It computes the per-row sums and the final FP64 tree
+ * of lbm_mass from a caller-owned buffer instead of a handle; rows are summed
+ * by one CTA each instead of lbm_mass's four column chunks, so the two agree
+ * to rounding, not bit for bit.
  *
  * g           geometry of the run: nx, ny, the plates (cap_x0, cap_x1, y_bot,
  *             y_top); solid_mask must be NULL (LBM_EINVAL otherwise); the
@@ -344,19 +346,33 @@ int lbm_load(const char* path, const lbm_options* opt, lbm_t** out);
  * mass        device double[2] receiving (M_A, M_B); caller-owned.
  * stream      cudaStream_t of the work (NULL = legacy default stream).
  *
- * Limit: ny <= LBM_NOALLOC_MAX_ROWS rows (LBM_EINVAL beyond it).  The per-row
- * partial sums live in one fixed device array of 2 * LBM_NOALLOC_MAX_ROWS
- * doubles (1 MiB) that every GPU loading the library holds until the process
- * exits.  All calls on a device share that array: calls whose work overlaps
- * on the GPU (different streams, or concurrent host threads) race and must
- * be serialised by the caller; a call overwrites every row it reads, so
- * nothing carries over from one call to the next.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  No memory is allocated or
- * freed.  Asynchronous; returns LBM_ECUDA if the look-up or a launch fails. */
+ * Limits (LBM_EINVAL beyond them, checked before anything is launched):
+ * ny <= LBM_NOALLOC_MAX_ROWS rows, and 18 * ny * pitch < 2^31 elements (the
+ * kernels index one buffer with 32-bit element offsets; lbm_create applies
+ * the same bound).  The per-row partial sums live in one fixed device array
+ * of 2 * LBM_NOALLOC_MAX_ROWS doubles (1 MiB) that every GPU loading the
+ * library holds until the process exits.  All calls on a device share that
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * concurrent host threads) race and must be serialised by the caller; a call
+ * writes every row sum it reads before reading it, so nothing carries over
+ * from one call to the next.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  No memory is allocated or freed.  Asynchronous;
+ * returns LBM_ECUDA if the look-up or a launch fails. */
 #define LBM_NOALLOC_MAX_ROWS 65536
 int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void* populations, int pitch,
                      const double rho_ref[2], double* mass, void* stream);
+
+/* Failure-path self-test of the bounded device waits (no counterpart in the
+ * paper).  Launches one CTA that waits, with the same bounded mbarrier wait as
+ * the ring-fed step kernels, on a phase that nothing completes, giving up
+ * after `cycles` SM clock cycles (1e3 .. 4e9; the step kernels use 2e9, about
+ * 1 s), and reports what a step would: LBM_ETIMEOUT when the wait ran out,
+ * LBM_OK if it completed, LBM_EINVAL for a cycle count out of range (nothing
+ * launched), LBM_ENOMEM / LBM_ECUDA on CUDA failures.  The kernel faults
+ * nothing and leaves the context usable; it synchronises `stream` (a
+ * cudaStream_t, NULL = default) and allocates and frees 4 bytes. */
+int lbm_selftest_wait_timeout(long long cycles, void* stream);
 
 /* Sticky device status of the handle (synchronises). */
 int lbm_status(lbm_t* h);

@@ -55,8 +55,6 @@ class RunInfo(ctypes.Structure):
 # name -> (restype, argtypes); every function declared in include/lbm.h
 SIGNATURES = {
     "lbm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong, c_void_p]),
-    "lbm_probe_stream": (ctypes.c_int, [ctypes.c_int, c_void_p, c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, c_void_p]),
     "lbm_default_options": (None, [P(Options)]),
     "lbm_create": (ctypes.c_int, [P(Geometry), c_double, P(c_double), c_double, c_double, P(Options),
                                   P(c_void_p)]),

@@ -35,7 +35,7 @@ UNITS = {
     "lbm_capi.cu": [],
     "mlp.cu": [],
     "lbm_noalloc.cu": [],
-    "stream_probe.cu": [],
+    "lbm_selftest.cu": [],
 }
 
 

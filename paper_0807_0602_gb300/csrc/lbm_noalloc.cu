@@ -3,9 +3,11 @@
 //
 // lbm_mass needs per-row partial sums between its two passes and keeps them
 // in device memory that lbm_create allocated.  Code that cannot allocate
-// device memory at the point where it needs the sums (see the header) gets
-// the same per-row sum and final tree here, with the partial sums in one
-// file-scope device array of fixed size, shared by every call on a device.
+// device memory at the point where it needs the sums (an allocator callback
+// that must not re-enter its allocator, a process whose device memory another
+// framework's pool already reserves) gets the same per-row sum and final tree
+// here, with the partial sums in one file-scope device array of fixed size,
+// shared by every call on a device.
 // lbm_mass splits each row into column chunks for parallelism; this variant
 // sums a whole row per CTA, so the two agree to rounding, not bit for bit.
 #include <mutex>
@@ -67,6 +69,8 @@ extern "C" int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void
     if (precision < LBM_F64 || precision > LBM_F16S) return LBM_EINVAL;
     if (g->nx < 1 || g->ny < 1 || pitch < g->nx) return LBM_EINVAL;
     if (g->ny > kMaxRows) return LBM_EINVAL;   // more rows than the static partial-sum array holds
+    // the row sums index the buffer with 32-bit element offsets ((9 + i) * plane + y * pitch + x)
+    if (18LL * g->ny * pitch >= (1LL << 31)) return LBM_EINVAL;
     if (g->solid_mask) return LBM_EINVAL;      // plates only: a mask would have to be copied to the device
     if (g->cap_x0 < 0 || g->cap_x1 < g->cap_x0 || g->cap_x1 > g->nx) return LBM_EINVAL;
     if (g->y_bot < -1 || g->y_bot >= g->ny || g->y_top < -1 || g->y_top >= g->ny) return LBM_EINVAL;
