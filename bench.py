@@ -49,9 +49,9 @@ WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 p
             "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
 BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
 KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
-           "node-tile", "bidirectional"]
+           "node-tile", "bidirectional", "ring"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
-                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir"]
+                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir", "k_step_ring"]
 # committed ncu summaries of the step kernel on this workload, by (variant, tile)
 # keyed by (kernel, tile, species): species None for alpha = 4/9, m = 1, else --species
 SPECIES_1_3 = (4.0 / 9.0, 0.8, 1.0, 25.0 / 9.0)

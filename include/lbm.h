@@ -297,9 +297,19 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         at most 1024 threads; nx >= 4);
  *   LBM_KERNEL_BIDIR      parked in shared memory, two groups of tile_w
  *                         threads marching away from the tile's middle row
- *                         (tile_w in {64, 128}, FP64 64).
- * depth is read by LBM_KERNEL_ASYNC and LBM_KERNEL_TMA and must be 4 for the
- * others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
+ *                         (tile_w in {64, 128}, FP64 64);
+ *   LBM_KERNEL_RING       a persistent grid of warp-specialised CTAs: one
+ *                         producer warp streams the source rows of a strip
+ *                         of 120 columns into a ring of `depth` row slots
+ *                         (3, 4 or 5) by bulk copies with mbarrier
+ *                         completion, two consumer warps collide two columns
+ *                         per thread in packed FP32; the CTAs draw row
+ *                         segments of the strips from a device counter.
+ *                         LBM_F32 and LBM_F16S only; tile_w must be 128 (the
+ *                         segment height is chosen by the library, tile_h is
+ *                         only recorded); nx >= 4.
+ * depth is read by LBM_KERNEL_ASYNC, LBM_KERNEL_TMA and LBM_KERNEL_RING and
+ * must be 4 for the others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */
 #define LBM_KERNEL_REGISTER 0
 #define LBM_KERNEL_ASYNC 1
@@ -312,6 +322,7 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
 #define LBM_KERNEL_TILE 8        /* one node per thread, W x (R + 2) tiles: W in {32, 64}, R in {6, 14, 30}
                                     (W = 64: R in {6, 14}); nx >= 4 */
 #define LBM_KERNEL_BIDIR 9       /* two thread groups marching away from the tile's middle row */
+#define LBM_KERNEL_RING 10       /* persistent producer/consumer ring of bulk-copied row slots (FP32, FP16S) */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 

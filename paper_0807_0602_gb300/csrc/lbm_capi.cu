@@ -52,7 +52,10 @@ struct lbm_s {
                                    // node, 5 register pull with bulk L2 prefetch of rows ahead, 6 register
                                    // pull with the pulled rows parked in shared memory, 7 two columns per
                                    // thread, 8 one node per thread over a W x (R + 2) tile, 9 two thread
-                                   // groups marching away from the tile's middle row
+                                   // groups marching away from the tile's middle row, 10 persistent
+                                   // producer/consumer ring of row slots filled by bulk copies
+    int* d_queue = nullptr;        // ring kernel: segment counter and finished-CTA counter
+    int ring_grid = 0;             // ring kernel: CTAs of the persistent grid
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -178,6 +181,41 @@ int validate_options(const lbm_options& o) {
 // x = nx); buffers point at column 0 of row 0.
 int round_pitch(int nx) { return (nx + 2 * LBM_COL0 + 63) / 64 * 64; }
 
+// Ring kernel (kvar 10): strips of kRingWc collided columns, cut into
+// segments of R rows that the persistent CTAs draw one by one.  R is chosen
+// so that the largest number of segments a CTA may have to take, times the
+// rows it pulls per segment (R + 2 with the halo rows), is smallest for a
+// grid of about G resident CTAs.
+void build_ring_tiles(lbm_t* h, int G) {
+    h->tiles.clear();
+    h->tile_begin.assign(h->nruns, 0);
+    h->tile_count.assign(h->nruns, 0);
+    int best_R = 1;
+    double best = 1e300;
+    for (int R : {4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 192, 256, 384, 512}) {
+        double items = 0.0, rows = 0.0;
+        for (const RunDesc& rd : h->runs) {
+            const int strips = (rd.nx + sc::kRingWc - 1) / sc::kRingWc;
+            const int chunks = (rd.ny + R - 1) / R;
+            items += (double)strips * chunks;
+            rows += (double)strips * (rd.ny + 2.0 * chunks);
+        }
+        const double per_cta = std::max(std::ceil(items / G) * (R + 2), rows / G);
+        if (per_cta < best * (1.0 - 1e-9)) {
+            best = per_cta;
+            best_R = R;
+        }
+    }
+    for (int r = 0; r < h->nruns; ++r) {
+        const RunDesc& rd = h->runs[r];
+        h->tile_begin[r] = (int)h->tiles.size();
+        for (int x0 = 0; x0 < rd.nx; x0 += sc::kRingWc)
+            for (int y0 = 0; y0 < rd.ny; y0 += best_R)
+                h->tiles.push_back({r, x0, y0, std::min(y0 + best_R, rd.ny)});
+        h->tile_count[r] = (int)h->tiles.size() - h->tile_begin[r];
+    }
+}
+
 void build_tiles(lbm_t* h, int W, int R) {
     h->tiles.clear();
     h->tile_begin.assign(h->nruns, 0);
@@ -201,8 +239,32 @@ void drop_graphs(lbm_t* h) {
     h->graphs.clear();
 }
 
+// Resident CTAs of the ring kernel with depth D on this device (all SMs).
+int ring_grid_size(lbm_t* h, int D, int* grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    CK(h, dispatch_step(h, [&](auto L) { return L.ring_ctas_per_sm(D, &per_sm); }));
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1 || sms < 1) return LBM_EINVAL;
+    *grid = per_sm * sms;
+    return LBM_OK;
+}
+
 int upload_tiles(lbm_t* h, int W, int R) {
-    build_tiles(h, W, R);
+    if (h->kvar == 10) {
+        int G = 0;
+        int rc = ring_grid_size(h, h->depth, &G);
+        if (rc) return rc;
+        build_ring_tiles(h, G);
+        h->ring_grid = G;
+        if (!h->d_queue) {
+            h->d_queue = static_cast<int*>(dalloc(h, 2 * sizeof(int)));
+            if (!h->d_queue) return LBM_ENOMEM;
+            CK(h, cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(int), h->stream));
+        }
+    } else {
+        build_tiles(h, W, R);
+    }
     const size_t need = h->tiles.size() * sizeof(Tile);
     if (need > h->d_tiles_cap) {
         // the old table may still be in use by queued work: keep it until destroy
@@ -253,11 +315,25 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     if (h->kvar == 8)
         return dispatch_step(h,
                              [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 10)
+        return dispatch_step(h, [&](auto L) {
+            return L.step_ring(h->depth, h->d_runs, h->d_tiles, nt, h->d_queue, h->ring_grid, parity, h->d_err, s);
+        });
     return dispatch_step(h, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
-    if (R < 1 || kvar < 0 || kvar > 9) return false;
+    if (R < 1 || kvar < 0 || kvar > 10) return false;
+    if (kvar == 10) {
+        // ring of `depth` row slots (3, 4 or 5) fed by bulk copies: FP32 and
+        // FP16S storage; strips of 120 columns (tile_w 128; the segment height
+        // is chosen by the library); the windows rely on two ghost columns
+        // each side: nx >= 4
+        if (h->precision == LBM_F64 || W != 128 || depth < 3 || depth > 5) return false;
+        for (const RunDesc& rd : h->runs)
+            if (rd.nx < 4) return false;
+        return true;
+    }
     if (kvar == 9) {
         // two groups of W threads, each staging 2 rows of 18 W populations
         // statically: W in {64, 128} (FP64: 64)
@@ -408,6 +484,8 @@ int autotune(lbm_t* h, int64_t* n) {
     for (int W : {32, 64})
         for (int R : {6, 14})
             if (schedule_ok(h, W, R, 8, 4)) cands.push_back({W, R, 8, 4});
+    for (int D : {3, 4, 5})
+        if (schedule_ok(h, 128, 4, 10, D)) cands.push_back({128, 4, 10, D});
     // pass 1: every candidate for `per` steps; pass 2: the kFinal fastest
     // again for 2 per steps each (candidates within a few per cent of each
     // other are told apart by the longer timing, not by the noise of pass 1)

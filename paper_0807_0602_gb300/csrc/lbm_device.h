@@ -77,6 +77,9 @@ inline void fill_coef_f32(RunDesc& rd) {
 // column chunks (CTAs) per row of the mass reduction
 constexpr int kMassChunks = 4;
 
+// collided columns per strip of the persistent ring kernel (LBM_KERNEL_RING)
+constexpr int kRingWc = 120;
+
 // opt-in shared memory per CTA on sm_103a (227 KB)
 constexpr size_t kMaxSmemPerCta = 232448;
 
@@ -129,6 +132,13 @@ struct Step {
                                   cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
+    // persistent ring kernel (FP32 / FP16S storage, D row slots): `grid` CTAs
+    // draw the ntiles segments from the counter pair `queue` (zero before the
+    // launch, zero again after it)
+    static cudaError_t step_ring(int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int* queue, int grid,
+                                 int parity, uint32_t* err, cudaStream_t s);
+    // resident CTAs per SM of that kernel (0 if not available)
+    static cudaError_t ring_ctas_per_sm(int D, int* out);
 };
 
 // Initialisation, observables, reductions and population transfers.

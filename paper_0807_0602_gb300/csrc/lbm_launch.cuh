@@ -6,6 +6,7 @@
 #include <atomic>
 
 #include "lbm_kernels.cuh"
+#include "lbm_ring.cuh"
 
 namespace sc {
 
@@ -215,6 +216,56 @@ cudaError_t Step<S, G>::step_bidir(int W, const RunDesc* d_runs, const Tile* d_t
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename S, int D, bool G>
+static cudaError_t ring_fn(const void** fn, int* smem, int* threads) {
+    if constexpr (sizeof(S) == 8) {
+        return cudaErrorInvalidValue;   // FP64 is arithmetic-bound: it keeps the register kernels
+    } else {
+        using RG = RingGeom<S, D>;
+        constexpr size_t bytes = RG::smem_bytes();
+        static_assert(bytes <= kMaxSmemPerCta, "ring slots exceed the shared memory of a CTA");
+        static std::atomic<unsigned long long> configured{0};   // per instantiation, one bit per device
+        const cudaError_t e = ensure_dynamic_smem((const void*)k_step_ring<S, D, G>, (int)bytes, configured);
+        if (e != cudaSuccess) return e;
+        *fn = (const void*)k_step_ring<S, D, G>;
+        *smem = (int)bytes;
+        *threads = RG::THREADS;
+        return cudaSuccess;
+    }
+}
+
+template <typename S, bool G>
+static cudaError_t ring_lookup(int D, const void** fn, int* smem, int* threads) {
+    switch (D) {
+        case 3: return ring_fn<S, 3, G>(fn, smem, threads);
+        case 4: return ring_fn<S, 4, G>(fn, smem, threads);
+        case 5: return ring_fn<S, 5, G>(fn, smem, threads);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S, bool G>
+cudaError_t Step<S, G>::ring_ctas_per_sm(int D, int* out) {
+    *out = 0;
+    const void* fn = nullptr;
+    int smem = 0, threads = 0;
+    cudaError_t e = ring_lookup<S, G>(D, &fn, &smem, &threads);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, threads, (size_t)smem);
+}
+
+template <typename S, bool G>
+cudaError_t Step<S, G>::step_ring(int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int* queue,
+                                  int grid, int parity, uint32_t* err, cudaStream_t s) {
+    if (grid <= 0 || ntiles <= 0) return cudaSuccess;
+    const void* fn = nullptr;
+    int smem = 0, threads = 0;
+    cudaError_t e = ring_lookup<S, G>(D, &fn, &smem, &threads);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&d_runs, (void*)&d_tiles, (void*)&ntiles, (void*)&queue, (void*)&parity, (void*)&err};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem, s);
 }
 
 template <typename S, bool G>

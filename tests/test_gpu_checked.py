@@ -41,6 +41,19 @@ for geom, prm in cases:
             M = lat.mass()
             assert np.array_equal(lat.populations(), ref.populations()), (geom, kern)
             assert np.all(np.abs(M - ref.mass()) <= 1e-12 * ref.mass())
+# the ring kernel (FP32 and FP16S storage only): its segments pass the same
+# checks, and it gives the default kernel's bits
+for geom, prm in cases:
+    nA, nB = W.random_fields(geom, 3, 0.2, 1.2)
+    run = dict(geom=geom, params=prm, init=("fields", nA, nB))
+    for prec in ("f32", "f16s"):
+        outs = []
+        for kw in (dict(), dict(tile=(128, 4), kernel=(10, 3))):
+            with Lattice(run, precision=prec, rho_ref=(1.0, 1.0), **kw) as lat:
+                lat.step(12)
+                lat.sync()
+                outs.append(lat.populations())
+        assert np.array_equal(outs[0].view(np.uint8), outs[1].view(np.uint8)), (geom, prec)
 print("checked build ok")
 '''
 
