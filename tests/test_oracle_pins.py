@@ -458,6 +458,68 @@ def test_capillary_front_follows_eq16_with_laplace_gamma_and_droplet_angle():
     assert 0.55 < ratio < 1.2
 
 
+def _phase_viscosity(nA, nB, tau_A, tau_B):
+    """Dynamic viscosity of a bulk phase of the mixture: the partial viscosities
+    n_k (tau_k - 1/2)/3 of the two species add (each species' momentum flux
+    relaxes with its own tau_k, Eq. 2)."""
+    return (nA * (tau_A - 0.5) + nB * (tau_B - 0.5)) / 3.0
+
+
+def test_capillary_front_with_viscous_gas_follows_the_viscous_law_of_eq15():
+    """Theoretical analysis, Eqs. 13-15 without inertia: the liquid column of
+    length z and the gas column of length L - z both resist, so
+    z' (mu_l z + mu_g (L - z)) = gamma H cos(theta) / 6, i.e.
+    F(z) = mu_g L z + (mu_l - mu_g) z^2 / 2 grows linearly in t.  With the gas
+    2.7 times more viscous than the liquid (tau_B = 2, tau_A = 1) the front
+    must speed up as the viscous gas column shortens, the viscous law must
+    fit z(t) better than a constant speed and than the single-fluid Washburn
+    form z^2 ~ t of Eq. 1, and the speed-up must not exceed the one the law
+    predicts between the same positions.  (Measured on the oracle: speed-up
+    1.26 against 1.67 predicted, residuals 0.36 / 0.45 / 2.27 lattice units.)
+    The viscosities are those of the two bulk phases read from the run, with
+    the partial viscosities of the species added."""
+    L, H, tA, tB = 64, 16, 1.0, 2.0
+    run = W.capillary_run_long_reservoir(L, H, 1.0, tA, tB, -0.3, 0.0)
+    o = oracle.OracleLattice(run["geom"], run["params"], *W.initial_fields(run))
+    ts, zs = [], []
+    nA = nB = None
+    while True:
+        ts.append(o.t)
+        zs.append(float(o.interface()[0]))
+        if o.t == 2000:           # phases settled; the front still far from the outlet
+            nA, nB = o.densities()
+        if zs[-1] >= 0.9 * L or o.t >= 30000:
+            break
+        o.step(200)
+    mid = (H + 2) // 2
+    mu_l = _phase_viscosity(nA[mid, 2 * L + 3], nB[mid, 2 * L + 3], tA, tB)     # liquid at the inlet
+    mu_g = _phase_viscosity(nA[mid, 3 * L - 3], nB[mid, 3 * L - 3], tA, tB)     # gas ahead of the front
+    assert nA[mid, 2 * L + 3] > 1.0 and nB[mid, 3 * L - 3] > 1.0 and mu_g > 2.0 * mu_l
+    t, z = np.array(ts, float), np.array(zs)
+    m = (t >= 1000) & (z < 0.9 * L)
+    t, z = t[m], z[m]
+    assert len(t) >= 20 and z[-1] > z[0] + L / 3.0          # the front travels a third of L
+    M = np.vstack([t, np.ones_like(t)]).T
+
+    def fit(y):
+        return np.linalg.lstsq(M, y, rcond=None)[0]
+
+    a, b = 0.5 * (mu_l - mu_g), mu_g * L
+    kF, cF = fit(b * z + a * z * z)
+    z15 = (-b + np.sqrt(b * b + 4 * a * (kF * t + cF))) / (2 * a)
+    kz, cz = fit(z)
+    kw, cw = fit(z * z)
+    rms15 = np.sqrt(np.mean((z15 - z) ** 2))
+    rms_lin = np.sqrt(np.mean((kz * t + cz - z) ** 2))
+    rms_w = np.sqrt(np.mean((np.sqrt(np.maximum(kw * t + cw, 0.0)) - z) ** 2))
+    assert kF > 0 and rms15 < rms_lin < rms_w
+    q = len(t) // 4
+    speed = np.diff(z) / np.diff(t)
+    up = speed[-q:].mean() / speed[:q].mean()
+    up_pred = (b + 2 * a * z[: q + 1].mean()) / (b + 2 * a * z[-q - 1:].mean())
+    assert 1.1 < up <= up_pred
+
+
 # ---- free alpha_k and molecular masses m_k (Model section, Eqs. 3-8) -------------
 
 @pytest.mark.parametrize("alpha", [0.2, 4.0 / 9.0, 0.8])

@@ -110,6 +110,19 @@ def capillary_run(L_cap: int, H: int, G: float, tau_A: float, tau_B: float, G_Aw
     return dict(geom=geom, params=params(G, tau_A, tau_B, G_Aw, G_Bw), init=("slab", L_cap // 2, x_front))
 
 
+def capillary_run_long_reservoir(L_cap: int, H: int, G: float, tau_A: float, tau_B: float, G_Aw: float,
+                                 G_Bw: float = 0.0) -> dict:
+    """Capillary of length L_cap at the right end of a 3 L_cap x (H + 2) box
+    whose reservoir (the left two thirds, periodic top and bottom) holds gas
+    on [0, L_cap/2) and liquid from L_cap/2 to the front at 2 L_cap + L_cap/4:
+    enough liquid to fill the whole capillary, so that the front can travel
+    its full length while the reservoir still feeds it."""
+    nx, ny = 3 * L_cap, H + 2
+    geom = capillary_geometry(nx, ny, 2 * L_cap, 3 * L_cap, 0, H + 1)
+    return dict(geom=geom, params=params(G, tau_A, tau_B, G_Aw, G_Bw),
+                init=("slab", L_cap // 2, 2 * L_cap + L_cap // 4))
+
+
 # ---- the five workload families ------------------------------------------
 
 def config_capillary_256x32() -> dict:
