@@ -43,6 +43,54 @@ def measure_angles(couplings, G, tau_A=1.0, tau_B=1.0, steps=8000, precision="f3
     return out
 
 
+def angle_table(G_values, tau_B_values, couplings, tau_A=1.0, steps=8000, precision="f32"):
+    """Contact angle theta(G, tau_B, G_Aw) of sessile droplets (G_Bw = 0) on
+    the grid G_values x tau_B_values x couplings, all droplets advanced in
+    one batched handle: the a-posteriori map from wall coupling to angle
+    (Model section, after Eq. 11).  Returns an array [len(G)][len(tau_B)][len(G_Aw)]."""
+    G_values, tau_B_values, couplings = (np.asarray(v, float) for v in (G_values, tau_B_values, couplings))
+    runs = [droplet_run(a, 0.0, G, tau_A, tB) for G in G_values for tB in tau_B_values for a in couplings]
+    out = np.full(len(runs), np.nan)
+    with Lattice(runs, precision=precision, tile=(128, 16)) as lat:
+        lat.step(steps)
+        for i in range(len(runs)):
+            nA, nB = lat.densities(i)
+            if np.all(np.isfinite(nA)) and np.all(np.isfinite(nB)):
+                out[i], _ = A.droplet_contact_angle(nA, nB, wall_y=0.5, skip_rows=3)
+    return out.reshape(len(G_values), len(tau_B_values), len(couplings))
+
+
+def coupling_for_angle(table, G_values, tau_B_values, couplings, G, tau_B, theta):
+    """Wall coupling G_Aw (G_Bw = 0) that gives the angle theta at (G, tau_B):
+    the angle is interpolated bilinearly in (G, tau_B) from the table, then
+    inverted linearly in G_Aw (theta increases with G_Aw).  Angles outside the
+    table's range give its end coupling."""
+    G_values, tau_B_values, couplings = (np.asarray(v, float) for v in (G_values, tau_B_values, couplings))
+
+    def frac(v, grid):
+        i = int(np.clip(np.searchsorted(grid, v) - 1, 0, len(grid) - 2))
+        return i, float(np.clip((v - grid[i]) / (grid[i + 1] - grid[i]), 0.0, 1.0))
+    i, fg = frac(G, G_values)
+    j, ft = frac(tau_B, tau_B_values)
+    th = ((1 - fg) * (1 - ft) * table[i, j] + fg * (1 - ft) * table[i + 1, j] + (1 - fg) * ft * table[i, j + 1]
+          + fg * ft * table[i + 1, j + 1])
+    order = np.argsort(th)
+    return float(np.interp(theta, th[order], couplings[order]))
+
+
+def map_couplings(runs, G_values=(1.0, 1.05, 1.1), tau_B_values=(1.0, 1.25, 1.5),
+                  couplings=(-0.5, -0.4, -0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3), steps=8000):
+    """Fills G_Aw of every run that carries params["theta_target"] from a
+    measured angle table; returns the table (G, tau_B, G_Aw grids and angles)."""
+    table = angle_table(G_values, tau_B_values, couplings, steps=steps)
+    for run in runs:
+        p = run["params"]
+        if "theta_target" in p:
+            p["G_Aw"] = coupling_for_angle(table, G_values, tau_B_values, couplings, p["G"], p["tau_B"],
+                                           p["theta_target"])
+    return dict(G=list(G_values), tau_B=list(tau_B_values), G_Aw=list(couplings), theta=table.tolist())
+
+
 def capillary_run(L_cap, H, G, tau_A, tau_B, G_Aw, G_Bw):
     """Capillary of length L_cap and height H in the right half of a
     2 L_cap x (H + 2) box; the reservoir holds gas and liquid (Fig. 1)."""

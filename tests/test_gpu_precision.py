@@ -69,6 +69,49 @@ def test_fp32_densities_within_1e5_after_1e4_steps(runs):
     assert rep["scale_rel_A"] <= 1e-5 and rep["scale_rel_B"] <= 1e-5
 
 
+def _front_bound(ref, dz=0.05):
+    """Largest density change a displacement of the fields by dz lattice units
+    can cause at each node: dz times the largest difference to a neighbour
+    (periodic), the FP64 field's local slope."""
+    g = np.zeros_like(ref)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dx or dy:
+                g = np.maximum(g, np.abs(np.roll(np.roll(ref, dy, 0), dx, 1) - ref))
+    return dz * g
+
+
+def test_fp32_density_error_after_1e4_steps_sits_at_the_fronts(runs):
+    """Where the FP32 density error of 10^4 steps lies.  A front that sits
+    0.05 lattice units from the FP64 one (the stated z(t) tolerance) moves the
+    densities next to it by up to 0.05 times their local slope; the test
+    records, per species, the worst error over 1e-5 max|n64| + 0.05 |grad n64|
+    (measured 0.93 for A, 2.6 for B), the error on flat nodes (slope below
+    1e-6 of the scale: 9.6e-6 and 2.6e-5 of the scale) and the median over
+    all fluid nodes (4.7e-7 and 4.2e-6).  Asserted: the median node is within
+    1e-5 of the scale, and the worst node is at least 50 times worse than the
+    worst flat node, i.e. the drift of FP32 concentrates at the moving fronts
+    and walls, not in the bulk phases."""
+    nA64, nB64, _, _ = runs["f64"]
+    nA, nB, _, _ = runs["f32"]
+    rep = {}
+    for name, a, ref in (("A", nA, nA64), ("B", nB, nB64)):
+        fluid = ref != 0
+        scale = np.abs(ref).max()
+        slope = _front_bound(ref)
+        err = np.abs(a - ref)
+        flat = fluid & (slope <= 1e-6 * scale)
+        rep[name] = dict(worst_over_bound=float((err / (1e-5 * scale + slope))[fluid].max()),
+                         worst_scale_rel=float(err[fluid].max() / scale), flat_nodes=int(flat.sum()),
+                         flat_scale_rel=float(err[flat].max() / scale),
+                         median_scale_rel=float(np.median(err[fluid]) / scale))
+    print("f32 density error by location:", json.dumps(rep))
+    for name in ("A", "B"):
+        r = rep[name]
+        assert r["median_scale_rel"] <= 1e-5
+        assert r["flat_nodes"] > 0 and r["worst_scale_rel"] >= 50.0 * r["flat_scale_rel"]
+
+
 def test_fp32_densities_within_1e5_after_100_steps():
     from paper_0807_0602_gb300.lbm import Lattice
     c = W.config_capillary_8192x160(tau_B=1.0)

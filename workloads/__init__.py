@@ -161,6 +161,31 @@ def batch_uneven_capillaries(n: int = 512, seed: int = 3) -> list:
             for r in range(n)]
 
 
+def batch_uneven_capillaries_stable(n: int = 512, seed: int = 3) -> list:
+    """The uneven ensemble of batch_uneven_capillaries inside the band where
+    the velocity-shift scheme stays finite for 2 10^4 steps and more: the
+    same sizes (H ~ U{16..128}, L_cap ~ U{256..4096}, grid 2 L_cap x (H + 2)),
+    G ~ U[1.0, 1.1], tau_A = 1, tau_B ~ U[1.0, 1.5] (gas up to 1.9 times more
+    viscous), and a target contact angle theta ~ U[60, 105] degrees per run
+    (the range that the stable couplings -0.5 <= G_Aw <= 0.3 reach at every G
+    and tau_B of the band).
+    The wall coupling G_Aw that gives theta is not drawn here: it comes from
+    a measured calibration table (the params carry G_Aw = nan and the target
+    under "theta_target")."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = rng.integers(16, 129, size=n)
+    L = rng.integers(256, 4097, size=n)
+    G = rng.uniform(1.0, 1.1, size=n)
+    tB = rng.uniform(1.0, 1.5, size=n)
+    th = rng.uniform(60.0, 105.0, size=n)
+    runs = []
+    for r in range(n):
+        run = capillary_run(int(L[r]), int(H[r]), float(G[r]), 1.0, float(tB[r]), float("nan"))
+        run["params"]["theta_target"] = float(th[r])
+        runs.append(run)
+    return runs
+
+
 def batch_sessile_droplets(n: int = 1024, seed: int = 4, nx: int = 256, ny: int = 128,
                            radius: float = 40.0) -> list:
     """n sessile droplets on a wall at y = 0 of a periodic nx x ny box, radius
