@@ -267,6 +267,24 @@ int lbm_mass(lbm_t* h, int run, double M[2]);
  * on_device as in lbm_densities. */
 int lbm_populations(lbm_t* h, int run, void* out, int on_device);
 
+/* Column windows of the populations of time t of run `run`, for the x-slab
+ * decomposition of one capillary over several lattices (a run too long for
+ * one GPU; the paper's Introduction notes that the lattice Boltzmann method
+ * parallelises naturally).  lbm_get_columns copies columns
+ * [x0, x0 + ncols) of all 18 populations and all rows into buf
+ * [2][9][ny][ncols] (storage precision, FP16S values as stored);
+ * lbm_set_columns overwrites those columns from buf (and the periodic images
+ * of columns 0, 1, nx - 2, nx - 1 that the ring kernels read), so that the
+ * next step pulls them.  A slab of width w owned columns is run as a
+ * lattice of w + 4 columns whose outer two columns on each side are set,
+ * after every step, to the neighbours' edge columns: every owned column then
+ * gets exactly the inputs it has in the undivided lattice (the pull reaches
+ * one column, the densities of the force one more).  0 <= x0,
+ * x0 + ncols <= nx, ncols >= 1 (LBM_EINVAL otherwise).  on_device as in
+ * lbm_densities (host buffers: the call synchronises). */
+int lbm_get_columns(lbm_t* h, int run, int x0, int ncols, void* buf, int on_device);
+int lbm_set_columns(lbm_t* h, int run, int x0, int ncols, const void* buf, int on_device);
+
 /* Tiling in use (CTA width, rows per CTA). */
 int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h);
 

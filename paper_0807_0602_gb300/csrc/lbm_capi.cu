@@ -939,6 +939,42 @@ int lbm_populations(lbm_t* h, int run, void* out, int on_device) {
     return LBM_OK;
 }
 
+// Column windows of the current populations (x-slab halo exchange).
+static int columns_io(lbm_t* h, int run, int x0, int ncols, void* buf, int on_device, bool write) {
+    if (check_run(h, run) || !buf) return LBM_EINVAL;
+    const RunDesc& rd = h->runs[run];
+    if (x0 < 0 || ncols < 1 || x0 > rd.nx - ncols) return LBM_EINVAL;
+    const size_t bytes = (size_t)18 * rd.ny * ncols * h->elem;
+    void* d = buf;
+    if (!on_device) {
+        if (!h->d_popscratch) {
+            h->d_popscratch = dalloc(h, (size_t)18 * h->max_nodes * h->elem);
+            if (!h->d_popscratch) return LBM_ENOMEM;
+        }
+        d = h->d_popscratch;
+        if (write) CK(h, cudaMemcpyAsync(d, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    }
+    const int parity = (int)(h->t & 1);
+    cudaError_t e = dispatch(h->precision, [&](auto L) {
+        return write ? L.set_cols(h->d_runs, run, parity, rd.ny, x0, ncols, d, h->stream)
+                     : L.get_cols(h->d_runs, run, parity, rd.ny, x0, ncols, d, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (!on_device) {
+        if (!write) CK(h, cudaMemcpyAsync(buf, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_get_columns(lbm_t* h, int run, int x0, int ncols, void* buf, int on_device) {
+    return columns_io(h, run, x0, ncols, buf, on_device, false);
+}
+
+int lbm_set_columns(lbm_t* h, int run, int x0, int ncols, const void* buf, int on_device) {
+    return columns_io(h, run, x0, ncols, const_cast<void*>(buf), on_device, true);
+}
+
 int lbm_get_tiling(const lbm_t* h, int* tile_w, int* tile_h) {
     if (!h || !tile_w || !tile_h) return LBM_EINVAL;
     *tile_w = h->tile_w;

@@ -156,6 +156,11 @@ struct Launch {
                                    cudaStream_t s);
     static cudaError_t import_pops(const RunDesc* d_runs, int run, int parity, int nx, int ny, const void* in,
                                    cudaStream_t s);
+    // column window [x0, x0 + ncols) to / from a packed [18][ny][ncols] buffer
+    static cudaError_t get_cols(const RunDesc* d_runs, int run, int parity, int ny, int x0, int ncols, void* out,
+                                cudaStream_t s);
+    static cudaError_t set_cols(const RunDesc* d_runs, int run, int parity, int ny, int x0, int ncols,
+                                const void* in, cudaStream_t s);
 };
 
 cudaError_t launch_log_advance(LogCtl lc, cudaStream_t s);

@@ -1907,6 +1907,43 @@ __global__ void k_import(const RunDesc* __restrict__ runs, int run, int parity, 
     }
 }
 
+// Populations of the column window [x0, x0 + ncols) (0 <= x0, x0 + ncols <= nx)
+// to / from a packed buffer [18][ny][ncols]; writes also refresh the ghost
+// images of columns 0, 1 and nx - 2, nx - 1 (the x-slab halo exchange).
+template <typename S>
+__global__ void k_get_cols(const RunDesc* __restrict__ runs, int run, int parity, int x0, int ncols,
+                           S* __restrict__ out) {
+    const RunDesc& rd = runs[run];
+    const S* base = static_cast<const S*>(rd.buf[parity]);
+    const long long per = (long long)rd.ny * ncols, total = 18 * per;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long ki = q / per;
+        const int rem = (int)(q - ki * per);
+        const int y = rem / ncols, x = x0 + (rem - y * ncols);
+        out[q] = base[ki * rd.plane + (long long)y * rd.pitch + x];
+    }
+}
+
+template <typename S>
+__global__ void k_set_cols(const RunDesc* __restrict__ runs, int run, int parity, int x0, int ncols,
+                           const S* __restrict__ in) {
+    const RunDesc& rd = runs[run];
+    S* base = static_cast<S*>(rd.buf[parity]);
+    const long long per = (long long)rd.ny * ncols, total = 18 * per;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long ki = q / per;
+        const int rem = (int)(q - ki * per);
+        const int y = rem / ncols, x = x0 + (rem - y * ncols);
+        S* p = base + ki * rd.plane + (long long)y * rd.pitch + x;
+        *p = in[q];
+        const int gr = ghost_r(x, rd.nx), gl = ghost_l(x, rd.nx);
+        if (gr) p[gr] = in[q];
+        if (gl) p[gl] = in[q];
+    }
+}
+
 // ---- fronts (Numerical Results section, Figs. 6-8) -------------------------
 // Four tracked rows per run, scanned from cap_x0:
 //   g = 0, 1: the centre row(s) with v = phi = (n_A - n_B)/(n_A + n_B);

@@ -332,4 +332,22 @@ cudaError_t Launch<S>::import_pops(const RunDesc* d_runs, int run, int parity, i
     return cudaGetLastError();
 }
 
+template <typename S>
+cudaError_t Launch<S>::get_cols(const RunDesc* d_runs, int run, int parity, int ny, int x0, int ncols, void* out,
+                                cudaStream_t s) {
+    const long long total = 18LL * ny * ncols;
+    k_get_cols<S><<<clamp_grid((total + 255) / 256, 4096), 256, 0, s>>>(d_runs, run, parity, x0, ncols,
+                                                                        static_cast<S*>(out));
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t Launch<S>::set_cols(const RunDesc* d_runs, int run, int parity, int ny, int x0, int ncols,
+                                const void* in, cudaStream_t s) {
+    const long long total = 18LL * ny * ncols;
+    k_set_cols<S><<<clamp_grid((total + 255) / 256, 4096), 256, 0, s>>>(d_runs, run, parity, x0, ncols,
+                                                                        static_cast<const S*>(in));
+    return cudaGetLastError();
+}
+
 }  // namespace sc

@@ -17,6 +17,18 @@ PRECISIONS = {"f64": L.LBM_F64, "f32": L.LBM_F32, "f16s": L.LBM_F16S}
 STORAGE_DTYPE = {L.LBM_F64: np.float64, L.LBM_F32: np.float32, L.LBM_F16S: np.float16}
 
 
+class _TorchDtypes(dict):
+    """torch dtype of the stored populations per precision code (torch is
+    imported on first use)."""
+    def __missing__(self, key):
+        import torch
+        self.update({L.LBM_F64: torch.float64, L.LBM_F32: torch.float32, L.LBM_F16S: torch.float16})
+        return self[key]
+
+
+TORCH_STORAGE_DTYPE = _TorchDtypes()
+
+
 class _TorchAllocator:
     """Device allocations through torch's caching allocator."""
 
@@ -273,6 +285,25 @@ class Lattice:
         out = np.empty((2, 9, ny, nx), dtype=STORAGE_DTYPE[self.precision])
         L.check(self._lib.lbm_populations(self._h, int(run), out.ctypes.data_as(ctypes.c_void_p), 0), "lbm_populations")
         return out
+
+    # ---- column windows (x-slab halo exchange) ---------------------------
+    def get_columns(self, x0: int, ncols: int, run: int = 0, out=None):
+        """Populations of columns [x0, x0 + ncols): a device tensor
+        [2, 9, ny, ncols] in the storage dtype (into `out` if given)."""
+        ny, _ = self.shapes[run]
+        if out is None:
+            out = self._torch.empty((2, 9, ny, int(ncols)), dtype=TORCH_STORAGE_DTYPE[self.precision],
+                                    device=f"cuda:{self.device}")
+        L.check(self._lib.lbm_get_columns(self._h, int(run), int(x0), int(ncols), ctypes.c_void_p(out.data_ptr()), 1),
+                "lbm_get_columns")
+        return out
+
+    def set_columns(self, x0: int, buf, run: int = 0) -> None:
+        """Overwrites columns [x0, x0 + ncols) from a contiguous device tensor
+        [2, 9, ny, ncols] in the storage dtype."""
+        assert buf.is_contiguous() and buf.is_cuda
+        L.check(self._lib.lbm_set_columns(self._h, int(run), int(x0), int(buf.shape[-1]),
+                                          ctypes.c_void_p(buf.data_ptr()), 1), "lbm_set_columns")
 
     # ---- checkpoints ---------------------------------------------------
     def save(self, path: str) -> None:
