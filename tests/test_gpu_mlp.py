@@ -56,7 +56,21 @@ def test_gradients_match_oracle_and_are_deterministic(net_mod):
     lb, gb = M.backward(th.astype(np.float64), X.astype(np.float64), T.astype(np.float64), bf16=True)
     assert abs(float(loss) - lb) <= 1e-3 * lb
     assert np.linalg.norm(g - gb) <= 2e-2 * np.linalg.norm(gb)
-    # per layer too (biases of the last layer are plain FP32 sums)
+    # element by element, per parameter block (each layer's weights and
+    # biases): the largest difference within 2e-2 of the block's largest
+    # gradient (a flipped bf16 rounding moves an element by one bf16 unit of
+    # an operand), and the median element within 1e-3 relative; a wrong or
+    # transposed block fails both
+    off = 0
+    for a, b in ((6, 128), (128, 128), (128, 128), (128, 3)):
+        for size in (a * b, b):
+            gk, bk = g[off:off + size], gb[off:off + size]
+            off += size
+            assert np.max(np.abs(gk - bk)) <= 2e-2 * np.max(np.abs(bk)), (a, b, size)
+            big = np.abs(bk) > 1e-3 * np.max(np.abs(bk))
+            assert np.median(np.abs(gk - bk)[big] / np.abs(bk)[big]) <= 1e-3, (a, b, size)
+    assert off == g.size
+    # the output layer's biases are plain FP32 sums of FP32 residuals
     assert np.allclose(g[-3:], gb[-3:], rtol=1e-3, atol=1e-7)
     net.close()
 
