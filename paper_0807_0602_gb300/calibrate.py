@@ -103,7 +103,9 @@ def capillary_run(L_cap, H, G, tau_A, tau_B, G_Aw, G_Bw):
 def capillary_prefactors(samples, L_cap=256, steps=20000, log_every=100, precision="f32", t_min=2000.0):
     """For each (G_Aw, G_Bw, G, tau_A, tau_B, H): the Washburn prefactor
     gamma H cos(theta) / (3 mu_l) obtained from the viscous front law of
-    Eq. 15 with both viscosities, and the prefactor a of the precursor lead
+    Eq. 15 with both viscosities (twice the slope of
+    phi = (mu_l - mu_g) z^2 / 2 + mu_g L z against t, t >= t_min, over mu_l),
+    and the prefactor a of the precursor lead
     z_prec - z_bulk = a t^(1/2).  Viscosities mu_k = rho nu_k with the total
     bulk density rho and nu_k = (tau_k - 1/2)/3."""
     runs = [capillary_run(L_cap, int(s[5]), s[2], s[3], s[4], s[0], s[1]) for s in samples]
@@ -122,10 +124,11 @@ def capillary_prefactors(samples, L_cap=256, steps=20000, log_every=100, precisi
             rho = RHO[0] + RHO[1]
             mu_l = rho * (s[3] - 0.5) / 3.0
             mu_g = rho * (s[4] - 0.5) / 3.0
-            z0 = zb[0]
-            phi = 0.5 * (mu_l - mu_g) * (zb ** 2 - z0 ** 2) + mu_g * L_cap * (zb - z0)
+            phi = 0.5 * (mu_l - mu_g) * zb ** 2 + mu_g * L_cap * zb
             m = t >= t_min
-            D = float((t[m] * phi[m]).sum() / (t[m] * t[m]).sum())   # = gamma H cos(theta) / 6
+            # slope of the straight line through phi(t) after the start-up
+            # transient (its intercept absorbs the transient's lag)
+            D = float(np.polyfit(t[m], phi[m], 1)[0])   # = gamma H cos(theta) / 6
             kw[i] = 2.0 * D / mu_l
             ap[i] = A.sqrt_prefactor(t, zp - zb, t_min)
     return kw, ap
