@@ -49,27 +49,31 @@ WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 p
             "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
 BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
 KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
-           "node-tile", "bidirectional", "ring"]
+           "node-tile", "bidirectional", "ring", "bidir-independent", "bidir-packed"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
-                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir", "k_step_ring"]
+                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir", "k_step_ring",
+                "k_step_bidir (independent groups)", "k_step_bidir_sp"]
 # committed ncu summaries of the step kernel on this workload, by (variant, tile)
 # keyed by (kernel, tile, species): species None for alpha = 4/9, m = 1, else --species
 SPECIES_1_3 = (4.0 / 9.0, 0.8, 1.0, 25.0 / 9.0)
 PROFILES = {
-    (6, (128, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
-    (6, (64, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
-    (9, (64, 8), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
-    (9, (64, 4), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x4_f32_capillary_8192x160.txt"),
-    (9, (64, 12), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x12_f32_capillary_8192x160.txt"),
-    (9, (64, 16), None): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x16_f32_capillary_8192x160.txt"),
-    (6, (256, 4), None): os.path.join(ROOT, "profiles", "k_step_smem_tile256x4_f32_capillary_8192x160.txt"),
-    (8, (32, 6), None): os.path.join(ROOT, "profiles", "k_step_tile_tile32x6_f32_capillary_8192x160.txt"),
-    (9, (64, 8), SPECIES_1_3): os.path.join(ROOT, "profiles",
-                                            "k_step_bidir_species_tile64x8_f32_capillary_8192x160.txt"),
+    (6, (128, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
+    (6, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 8), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
+    (9, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 12), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x12_f32_capillary_8192x160.txt"),
+    (9, (64, 16), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x16_f32_capillary_8192x160.txt"),
+    (6, (256, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile256x4_f32_capillary_8192x160.txt"),
+    (8, (32, 6), None, "f32"): os.path.join(ROOT, "profiles", "k_step_tile_tile32x6_f32_capillary_8192x160.txt"),
+    (10, (128, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_ring_depth4_f32_capillary_8192x160.txt"),
+    (9, (64, 8), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f16s_capillary_8192x160.txt"),
+    (6, (128, 4), None, "f64"): os.path.join(ROOT, "profiles", "k_step_smem_tile128x4_f64_capillary_8192x160.txt"),
+    (9, (64, 8), SPECIES_1_3, "f32"): os.path.join(ROOT, "profiles",
+                                                   "k_step_bidir_species_tile64x8_f32_capillary_8192x160.txt"),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
-                  for f in ("lbm_kernels.cuh", "lbm_launch.cuh", "kernels_f32.cu", "kernels_gen_f32.cu",
-                            "lbm_device.h")]
+                  for f in ("lbm_kernels.cuh", "lbm_packed.cuh", "lbm_ring.cuh", "lbm_launch.cuh", "kernels_f32.cu",
+                            "kernels_gen_f32.cu", "lbm_device.h")]
 
 
 # (alpha_A, alpha_B, m_A, m_B) of --species, or None for alpha = 4/9, m = 1
@@ -92,11 +96,11 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic(kvar: int, tile):
+def read_traffic(kvar: int, tile, precision: str = "f32"):
     """DRAM bytes per step-kernel launch from the committed ncu summary of
-    this kernel variant and tile, or None if there is none or the kernel
-    sources changed since the counters were taken."""
-    key = (int(kvar), (int(tile[0]), int(tile[1])), SPECIES)
+    this kernel variant, tile and precision, or None if there is none or the
+    kernel sources changed since the counters were taken."""
+    key = (int(kvar), (int(tile[0]), int(tile[1])), SPECIES, precision)
     if key not in PROFILES:
         return None
     try:
@@ -789,7 +793,7 @@ def main():
     peak, peak_kind = peaks()
     alg_bytes = fluid_nodes * BYTES_PER_NODE[args.precision]
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    traffic = read_traffic(sched[2], sched[:2]) if args.precision == "f32" else None
+    traffic = read_traffic(sched[2], sched[:2], args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
                 "kernel": f"{KERNEL_NAMES[sched[2]]} (tile {sched[0]}x{sched[1]})",

@@ -325,7 +325,16 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         segments of the strips from a device counter.
  *                         LBM_F32 and LBM_F16S only; tile_w must be 128 (the
  *                         segment height is chosen by the library, tile_h is
- *                         only recorded); nx >= 4.
+ *                         only recorded); nx >= 4;
+ *   LBM_KERNEL_BIDIR_IND  LBM_KERNEL_BIDIR whose two groups, after their
+ *                         first rows, wait at barriers of their own, so that
+ *                         their load and arithmetic phases drift apart (same
+ *                         tile shapes);
+ *   LBM_KERNEL_BIDIR_SP   the bidirectional march with species A and B in
+ *                         the two lanes of packed FP32 instructions (FP32 and
+ *                         FP16S storage, tile_w in {64, 128}, any tile_h);
+ *                         each lane rounds as the scalar operation, so the
+ *                         populations equal the other kernels' bit for bit.
  * depth is read by LBM_KERNEL_ASYNC, LBM_KERNEL_TMA and LBM_KERNEL_RING and
  * must be 4 for the others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */
@@ -341,6 +350,8 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
                                     (W = 64: R in {6, 14}); nx >= 4 */
 #define LBM_KERNEL_BIDIR 9       /* two thread groups marching away from the tile's middle row */
 #define LBM_KERNEL_RING 10       /* persistent producer/consumer ring of bulk-copied row slots (FP32, FP16S) */
+#define LBM_KERNEL_BIDIR_IND 11  /* the bidirectional march, groups synchronised separately after step 0 */
+#define LBM_KERNEL_BIDIR_SP 12   /* the bidirectional march, both species in packed FP32 pairs (FP32, FP16S) */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 
@@ -402,6 +413,15 @@ int lbm_mass_noalloc(const lbm_geometry* g, int precision, const void* populatio
  * nothing and leaves the context usable; it synchronises `stream` (a
  * cudaStream_t, NULL = default) and allocates and frees 4 bytes. */
 int lbm_selftest_wait_timeout(long long cycles, void* stream);
+
+/* Measured FP64 fused multiply-add rate of the current device (no
+ * counterpart in the paper): a kernel of independent DFMA chains on every SM,
+ * timed with CUDA events after one warm-up launch; *flops_per_s receives
+ * 2 x DFMAs per second.  The denominator of the FP64 step's arithmetic
+ * roofline (the FP64 build is bound by GB300's FP64 pipe, not by HBM).
+ * Synchronises `stream`; allocates and frees a few bytes; LBM_ECUDA on
+ * CUDA failures. */
+int lbm_selftest_fp64_rate(double* flops_per_s, void* stream);
 
 /* Sticky device status of the handle (synchronises). */
 int lbm_status(lbm_t* h);

@@ -56,6 +56,7 @@ class RunInfo(ctypes.Structure):
 SIGNATURES = {
     "lbm_get_columns": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_void_p, ctypes.c_int]),
     "lbm_set_columns": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_void_p, ctypes.c_int]),
+    "lbm_selftest_fp64_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), c_void_p]),
     "lbm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong, c_void_p]),
     "lbm_default_options": (None, [P(Options)]),
     "lbm_create": (ctypes.c_int, [P(Geometry), c_double, P(c_double), c_double, c_double, P(Options),

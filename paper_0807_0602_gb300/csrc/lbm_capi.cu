@@ -53,7 +53,8 @@ struct lbm_s {
                                    // pull with the pulled rows parked in shared memory, 7 two columns per
                                    // thread, 8 one node per thread over a W x (R + 2) tile, 9 two thread
                                    // groups marching away from the tile's middle row, 10 persistent
-                                   // producer/consumer ring of row slots filled by bulk copies
+                                   // producer/consumer ring of row slots filled by bulk copies, 11 the
+                                   // bidirectional march with both species in packed FP32 pairs
     int* d_queue = nullptr;        // ring kernel: segment counter and finished-CTA counter
     int ring_grid = 0;             // ring kernel: CTAs of the persistent grid
     std::vector<int2> rows;
@@ -311,7 +312,7 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     if (h->kvar == 7)
         return dispatch_step(h, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 9)
-        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, false, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 8)
         return dispatch_step(h,
                              [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
@@ -319,11 +320,18 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
         return dispatch_step(h, [&](auto L) {
             return L.step_ring(h->depth, h->d_runs, h->d_tiles, nt, h->d_queue, h->ring_grid, parity, h->d_err, s);
         });
+    if (h->kvar == 11)
+        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, true, h->d_runs, h->d_tiles, nt, parity, s); });
+    if (h->kvar == 12)
+        return dispatch_step(h, [&](auto L) { return L.step_bidir_sp(W, h->d_runs, h->d_tiles, nt, parity, s); });
     return dispatch_step(h, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
-    if (R < 1 || kvar < 0 || kvar > 10) return false;
+    if (R < 1 || kvar < 0 || kvar > 12) return false;
+    if (kvar == 12)   // the species-packed bidirectional march: FP32 arithmetic, W in {64, 128}
+        return depth == 4 && (W == 64 || W == 128) && h->precision != LBM_F64;
+    if (kvar == 11) kvar = 9;   // the bidirectional march with independent groups
     if (kvar == 10) {
         // ring of `depth` row slots (3, 4 or 5) fed by bulk copies: FP32 and
         // FP16S storage; strips of 120 columns (tile_w 128; the segment height
@@ -479,7 +487,7 @@ int autotune(lbm_t* h, int64_t* n) {
     std::vector<Cand> cands;
     for (int W : {64, 128, 256})
         for (int R : Rs)
-            for (int kvar : {6, 9, 0, 5, 3, 7, 2})
+            for (int kvar : {6, 9, 11, 0, 5, 3, 7, 2})
                 if (schedule_ok(h, W, R, kvar, 4)) cands.push_back({W, R, kvar, 4});
     for (int W : {32, 64})
         for (int R : {6, 14})

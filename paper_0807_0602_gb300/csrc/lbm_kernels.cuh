@@ -912,16 +912,31 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
 // ... down to the halo row y1 and collides m ... y1 - 1.  The two groups
 // share their first rows through shared memory, so a tile of R rows pulls
 // R + 2 rows in R / 2 + 1 steps (k_step_smem: R + 2 steps).  Step k: pull,
-// barrier, collide; density slot of step k = group * 4 + (k & 3).
+// barrier, collide.
+// IND: the groups synchronise separately after step 0 (named barriers of W
+// threads), so that their load and arithmetic phases drift apart instead of
+// alternating in lock step.  Only the rows of step 0 are read by the other
+// group (at its step 1): they get slots of their own, never reused within
+// the tile, and the step-0 barrier is CTA-wide; density slots of step k >= 1
+// then rotate over 4 per group: group * 5 + 1 + ((k - 1) & 3).
+// Without IND: one CTA-wide barrier per step, slot group * 4 + (k & 3).
 template <typename S, int W>
 constexpr int kBidirMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 512 / W;   // 64 registers
 
-template <typename S, int W, bool G>
+// bar.sync on barrier 1 or 2 (immediate ids: the kernel reserves three barriers) for N threads
+template <int N>
+__device__ __forceinline__ void bar_group(int g) {
+    if (g == 0) asm volatile("bar.sync 1, %0;\n" ::"n"(N) : "memory");
+    else asm volatile("bar.sync 2, %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename S, int W, bool G, bool IND>
 __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(const RunDesc* __restrict__ runs,
                                                                               const Tile* __restrict__ tiles,
                                                                               int parity) {
     using C = typename Prec<S>::C;
-    __shared__ C sd[8][2][W];        // [group * 4 + step ring][species][column]
+    constexpr int NS = IND ? 5 : 4;   // density slots per group
+    __shared__ C sd[2 * NS][2][W];   // [group * NS + step slot][species][column]
     __shared__ C ps[2][2][18][W];    // [group][step parity][population][column]
 
     const Tile tl = tiles[blockIdx.x];
@@ -942,6 +957,7 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
     const int nsteps = (y1 - y0 + 1) / 2 + 1;                // same for both groups (U has the larger half)
     // row pulled by this group at step k (the last one is the halo row)
     auto row_at = [&](int k) { return grp_d == 0 ? m - 1 - k : m + k; };
+    auto slot = [&](int g, int k) { return IND ? g * NS + (k == 0 ? 0 : 1 + ((k - 1) & 3)) : g * NS + (k & 3); };
 
     auto pull = [&](int k, unsigned& smask) {
         const int r = row_at(k);
@@ -966,23 +982,25 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
                 }
             }
         }
-        sd[grp_d * 4 + (k & 3)][0][t] = nA;
-        sd[grp_d * 4 + (k & 3)][1][t] = nB;
+        sd[slot(grp_d, k)][0][t] = nA;
+        sd[slot(grp_d, k)][1][t] = nB;
     };
 
     unsigned sm_prev = 0, sm_cur = 0;
     for (int k = 0; k < nsteps; ++k) {
         // this group pulls rows 0 .. nrows (the last is its halo row)
         if (k <= nrows) pull(k, sm_cur);
-        __syncthreads();
+        if (!IND || k == 0)
+            __syncthreads();
+        else
+            bar_group<W>(grp_d);
         // collide the row pulled at step k - 1: U row m - k, D row m + k - 1
         if (k >= 1 && k <= nrows && sc.coll && !SOL(sm_prev, 0, 0)) {
             const int r = grp_d == 0 ? m - k : m + k - 1;
-            const int own = grp_d * 4, other = (1 - grp_d) * 4;
             // rows r - 1, r, r + 1 as density slots: the row beyond the middle at k = 1
             // is the other group's step-0 row
-            const int s_new = own + (k & 3), s_row = own + ((k - 1) & 3);
-            const int s_old = k >= 2 ? own + ((k - 2) & 3) : other;
+            const int s_new = slot(grp_d, k), s_row = slot(grp_d, k - 1);
+            const int s_old = k >= 2 ? slot(grp_d, k - 2) : slot(1 - grp_d, 0);
             const int s_m = grp_d == 0 ? s_new : s_old, s_p = grp_d == 0 ? s_old : s_new;
             C fc[2][9];
 #pragma unroll

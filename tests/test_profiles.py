@@ -21,15 +21,17 @@ def _kv(path):
 
 def test_bench_profile_table_points_at_matching_summaries():
     import bench
-    for (kvar, tile, species), path in bench.PROFILES.items():
+    for (kvar, tile, species, precision), path in bench.PROFILES.items():
         assert os.path.exists(path), path
         kv = _kv(path)
         assert kv["tile"] == f"{tile[0]}x{tile[1]}", path
         assert int(kv["dram_bytes_per_launch"]) > 0
         assert len(kv["kernel_hash"]) == 16
         name = os.path.basename(path)
-        assert name.startswith({2: "k_step_tma", 6: "k_step_smem", 8: "k_step_tile", 9: "k_step_bidir"}[kvar]), name
+        assert name.startswith({2: "k_step_tma", 6: "k_step_smem", 8: "k_step_tile", 9: "k_step_bidir",
+                                10: "k_step_ring"}[kvar]), name
         assert ("species" in name) == (species is not None), name
+        assert f"_{precision}_" in name, name
 
 
 def test_every_summary_states_its_command_from_committed_files():
