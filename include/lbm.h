@@ -115,10 +115,12 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  * log_capacity  records kept per run (a ring: the newest log_capacity).
  * autotune      1 = time the candidate tilings during the first lbm_step
  *               call long enough for them (every candidate for 6 steps,
- *               the 3 fastest again for 12; about 570 steps on a large
- *               grid) and keep the fastest.  These are real steps: tilings
- *               change only the schedule, and results are bit-identical for
- *               every tiling.
+ *               the 4 fastest again for 32; about 750 steps on a large
+ *               grid) and keep the fastest.  The candidates include, for
+ *               the bidirectional march, the tile heights whose tiles fill
+ *               one or two waves of resident CTAs.  These are real steps:
+ *               tilings change only the schedule, and results are
+ *               bit-identical for every tiling.
  * tile_w        CTA width (64, 128 or 256 threads; 0 = default 128);
  * tile_h        rows marched per CTA (0 = default 4, clamped to ny).
  *               The step kernel starts as LBM_KERNEL_SMEM where it takes the
@@ -314,7 +316,8 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         threads (tile_w in {32, 64}, tile_h in {6, 14, 30},
  *                         at most 1024 threads; nx >= 4);
  *   LBM_KERNEL_BIDIR      parked in shared memory, two groups of tile_w
- *                         threads marching away from the tile's middle row
+ *                         threads marching away from the tile's middle row,
+ *                         each at barriers of its own after the first rows
  *                         (tile_w in {64, 128}, FP64 64);
  *   LBM_KERNEL_RING       a persistent grid of warp-specialised CTAs: one
  *                         producer warp streams the source rows of a strip
@@ -325,16 +328,7 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         segments of the strips from a device counter.
  *                         LBM_F32 and LBM_F16S only; tile_w must be 128 (the
  *                         segment height is chosen by the library, tile_h is
- *                         only recorded); nx >= 4;
- *   LBM_KERNEL_BIDIR_IND  LBM_KERNEL_BIDIR whose two groups, after their
- *                         first rows, wait at barriers of their own, so that
- *                         their load and arithmetic phases drift apart (same
- *                         tile shapes);
- *   LBM_KERNEL_BIDIR_SP   the bidirectional march with species A and B in
- *                         the two lanes of packed FP32 instructions (FP32 and
- *                         FP16S storage, tile_w in {64, 128}, any tile_h);
- *                         each lane rounds as the scalar operation, so the
- *                         populations equal the other kernels' bit for bit.
+ *                         only recorded); nx >= 4.
  * depth is read by LBM_KERNEL_ASYNC, LBM_KERNEL_TMA and LBM_KERNEL_RING and
  * must be 4 for the others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */
@@ -350,9 +344,15 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
                                     (W = 64: R in {6, 14}); nx >= 4 */
 #define LBM_KERNEL_BIDIR 9       /* two thread groups marching away from the tile's middle row */
 #define LBM_KERNEL_RING 10       /* persistent producer/consumer ring of bulk-copied row slots (FP32, FP16S) */
-#define LBM_KERNEL_BIDIR_IND 11  /* the bidirectional march, groups synchronised separately after step 0 */
-#define LBM_KERNEL_BIDIR_SP 12   /* the bidirectional march, both species in packed FP32 pairs (FP32, FP16S) */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
+/* The autotuner's finalists (the paper has no counterpart: this reports on the
+ * library's own schedule search).  *count = number of finalists (0 before
+ * tuning has run); the first min(max, *count) are written: sched[4 j ..
+ * 4 j + 3] = (tile_w, tile_h, kernel, depth) of finalist j, ms_per_step[j] =
+ * its best per-step time over the final rounds, measured on back-to-back
+ * steps.  Host memory, caller-owned; no device work.  LBM_EINVAL for a null
+ * handle or count, or max > 0 with a null array. */
+int lbm_get_tuning(const lbm_t* h, int max, int* sched, float* ms_per_step, int* count);
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth);
 
 /* Writes a checkpoint (header, parameters, populations of time t, log) to

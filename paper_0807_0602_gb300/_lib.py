@@ -79,6 +79,8 @@ SIGNATURES = {
     "lbm_get_schedule": (ctypes.c_int, [c_void_p, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                                         P(ctypes.c_int)]),
     "lbm_set_schedule": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_get_tuning": (ctypes.c_int, [c_void_p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_float),
+                                      P(ctypes.c_int)]),
     "lbm_save": (ctypes.c_int, [c_void_p, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [ctypes.c_char_p, P(Options), P(c_void_p)]),
     "lbm_mass_noalloc": (ctypes.c_int, [P(Geometry), ctypes.c_int, c_void_p, ctypes.c_int, P(c_double), c_void_p,

@@ -53,8 +53,7 @@ struct lbm_s {
                                    // pull with the pulled rows parked in shared memory, 7 two columns per
                                    // thread, 8 one node per thread over a W x (R + 2) tile, 9 two thread
                                    // groups marching away from the tile's middle row, 10 persistent
-                                   // producer/consumer ring of row slots filled by bulk copies, 11 the
-                                   // bidirectional march with both species in packed FP32 pairs
+                                   // producer/consumer ring of row slots filled by bulk copies
     int* d_queue = nullptr;        // ring kernel: segment counter and finished-CTA counter
     int ring_grid = 0;             // ring kernel: CTAs of the persistent grid
     std::vector<int2> rows;
@@ -77,6 +76,8 @@ struct lbm_s {
     std::vector<Alloc> allocs;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     bool tuned = false;
+    std::vector<int> tune_sched;   // the tuner's finalists, 4 ints each (tile_w, tile_h, kernel, depth)
+    std::vector<float> tune_ms;    // and their best ms per step over the final rounds
     int sticky = LBM_OK;
 };
 
@@ -312,7 +313,7 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
     if (h->kvar == 7)
         return dispatch_step(h, [&](auto L) { return L.step_pair(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 9)
-        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, false, h->d_runs, h->d_tiles, nt, parity, s); });
+        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, h->d_runs, h->d_tiles, nt, parity, s); });
     if (h->kvar == 8)
         return dispatch_step(h,
                              [&](auto L) { return L.step_tile(W, h->tile_h, h->d_runs, h->d_tiles, nt, parity, s); });
@@ -320,18 +321,11 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
         return dispatch_step(h, [&](auto L) {
             return L.step_ring(h->depth, h->d_runs, h->d_tiles, nt, h->d_queue, h->ring_grid, parity, h->d_err, s);
         });
-    if (h->kvar == 11)
-        return dispatch_step(h, [&](auto L) { return L.step_bidir(W, true, h->d_runs, h->d_tiles, nt, parity, s); });
-    if (h->kvar == 12)
-        return dispatch_step(h, [&](auto L) { return L.step_bidir_sp(W, h->d_runs, h->d_tiles, nt, parity, s); });
     return dispatch_step(h, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
-    if (R < 1 || kvar < 0 || kvar > 12) return false;
-    if (kvar == 12)   // the species-packed bidirectional march: FP32 arithmetic, W in {64, 128}
-        return depth == 4 && (W == 64 || W == 128) && h->precision != LBM_F64;
-    if (kvar == 11) kvar = 9;   // the bidirectional march with independent groups
+    if (R < 1 || kvar < 0 || kvar > 10) return false;
     if (kvar == 10) {
         // ring of `depth` row slots (3, 4 or 5) fed by bulk copies: FP32 and
         // FP16S storage; strips of 120 columns (tile_w 128; the segment height
@@ -470,6 +464,36 @@ int advance(lbm_t* h, int64_t n) {
     return LBM_OK;
 }
 
+// Tiles of the bidirectional march with strips of W - 2 columns and R rows.
+long long bidir_tiles(const lbm_t* h, int W, int R) {
+    long long n = 0;
+    for (const RunDesc& rd : h->runs) n += (long long)((rd.nx + W - 3) / (W - 2)) * ((rd.ny + R - 1) / R);
+    return n;
+}
+
+// Smallest tile height whose bidirectional tiles fit in `waves` waves of
+// resident CTAs on this device, or 0 (none, or the occupancy is unknown).
+int wave_height(lbm_t* h, int W, int waves) {
+    int per_sm = 0, dev = 0, sms = 0;
+    if (dispatch_step(h, [&](auto L) { return L.bidir_ctas_per_sm(W, &per_sm); }) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const long long slots = (long long)waves * per_sm * sms;
+    int maxny = 1;
+    for (const RunDesc& rd : h->runs) maxny = std::max(maxny, rd.ny);
+    if (slots < 1 || bidir_tiles(h, W, maxny) > slots) return 0;
+    int lo = 1, hi = maxny;   // bidir_tiles falls as R grows: the first R that fits
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (bidir_tiles(h, W, mid) <= slots) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 // Times candidate tilings on the live state: the steps taken are real steps
 // (every tiling computes the same bits), only their schedule differs.
 int autotune(lbm_t* h, int64_t* n) {
@@ -487,18 +511,30 @@ int autotune(lbm_t* h, int64_t* n) {
     std::vector<Cand> cands;
     for (int W : {64, 128, 256})
         for (int R : Rs)
-            for (int kvar : {6, 9, 11, 0, 5, 3, 7, 2})
+            for (int kvar : {6, 9, 0, 5, 3, 7, 2})
                 if (schedule_ok(h, W, R, kvar, 4)) cands.push_back({W, R, kvar, 4});
+    // the bidirectional march also with the tile heights whose tiles fill one
+    // or two waves of resident CTAs exactly (a partial last wave leaves SMs idle)
+    for (int W : {64, 128}) {
+        for (int waves : {1, 2}) {
+            const int R = wave_height(h, W, waves);
+            if (R > 0 && std::find(Rs.begin(), Rs.end(), R) == Rs.end() && schedule_ok(h, W, R, 9, 4))
+                cands.push_back({W, R, 9, 4});
+        }
+    }
     for (int W : {32, 64})
         for (int R : {6, 14})
             if (schedule_ok(h, W, R, 8, 4)) cands.push_back({W, R, 8, 4});
     for (int D : {3, 4, 5})
         if (schedule_ok(h, 128, 4, 10, D)) cands.push_back({128, 4, 10, D});
-    // pass 1: every candidate for `per` steps; pass 2: the kFinal fastest
-    // again for 2 per steps each (candidates within a few per cent of each
-    // other are told apart by the longer timing, not by the noise of pass 1)
-    const int per = 6, kFinal = 3;
-    const int64_t need = (int64_t)cands.size() * (per + 1) + (int64_t)kFinal * (2 * per + 1);
+    // pass 1: every candidate for `per` steps; pass 2: the kFinal fastest in
+    // `rounds` interleaved rounds of per_final steps each, scored by their
+    // best round (candidates within a few per cent of each other are told
+    // apart by the longer timing, and a slow drift of the clock hits every
+    // finalist alike)
+    const int per = 6, kFinal = 4, per_final = 32, rounds = 3;
+    const int64_t need =
+        (int64_t)cands.size() * (per + 1) + (int64_t)rounds * kFinal * (per_final + 1);
     if (*n < need) return LBM_OK;  // too short to tune now
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
@@ -533,15 +569,26 @@ int autotune(lbm_t* h, int64_t* n) {
         if (!rc) pass1.push_back({ms, i});
     }
     Cand bw = {h->tile_w, h->tile_h, h->kvar, h->depth};
+    h->tune_sched.clear();
+    h->tune_ms.clear();
     if (!rc) {
         std::sort(pass1.begin(), pass1.end());
+        const int nf = std::min(kFinal, (int)pass1.size());
+        std::vector<float> fbest(nf, 1e30f);
+        for (int round = 0; round < rounds && !rc; ++round)
+            for (int j = 0; j < nf && !rc; ++j) {
+                float ms = 0.f;
+                time_cand(cands[pass1[j].second], per_final, ms);
+                if (!rc) fbest[j] = std::min(fbest[j], ms);
+            }
         float best = 1e30f;
-        for (int j = 0; j < kFinal && j < (int)pass1.size() && !rc; ++j) {
-            float ms = 0.f;
-            time_cand(cands[pass1[j].second], 2 * per, ms);
-            if (!rc && ms < best) {
-                best = ms;
-                bw = cands[pass1[j].second];
+        for (int j = 0; j < nf && !rc; ++j) {
+            const Cand& c = cands[pass1[j].second];
+            h->tune_sched.insert(h->tune_sched.end(), {c.W, c.R, c.kvar, c.depth});
+            h->tune_ms.push_back(fbest[j]);
+            if (fbest[j] < best) {
+                best = fbest[j];
+                bw = c;
             }
         }
     }
@@ -1008,6 +1055,17 @@ int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int*
     *tile_h = h->tile_h;
     *kernel = h->kvar;
     *depth = h->depth;
+    return LBM_OK;
+}
+
+int lbm_get_tuning(const lbm_t* h, int max, int* sched, float* ms_per_step, int* count) {
+    if (!h || max < 0 || !count || (max > 0 && (!sched || !ms_per_step))) return LBM_EINVAL;
+    const int n = (int)h->tune_ms.size();
+    *count = n;
+    for (int j = 0; j < n && j < max; ++j) {
+        for (int q = 0; q < 4; ++q) sched[4 * j + q] = h->tune_sched[4 * j + q];
+        ms_per_step[j] = h->tune_ms[j];
+    }
     return LBM_OK;
 }
 

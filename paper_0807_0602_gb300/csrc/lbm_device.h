@@ -128,9 +128,8 @@ struct Step {
                                  cudaStream_t s);
     static cudaError_t step_tile(int W, int R, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                  cudaStream_t s);
-    // ind: the two groups synchronise separately after their first rows
-    static cudaError_t step_bidir(int W, bool ind, const RunDesc* d_runs, const Tile* d_tiles, int ntiles,
-                                  int parity, cudaStream_t s);
+    static cudaError_t step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s);
     static cudaError_t moments(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
                                MomOut out, cudaStream_t s);
     // persistent ring kernel (FP32 / FP16S storage, D row slots): `grid` CTAs
@@ -140,9 +139,8 @@ struct Step {
                                  int parity, uint32_t* err, cudaStream_t s);
     // resident CTAs per SM of that kernel (0 if not available)
     static cudaError_t ring_ctas_per_sm(int D, int* out);
-    // species-packed bidirectional march (FP32 and FP16S storage, W in {64, 128})
-    static cudaError_t step_bidir_sp(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
-                                     cudaStream_t s);
+    // resident CTAs per SM of the bidirectional march with strips of W threads
+    static cudaError_t bidir_ctas_per_sm(int W, int* out);
 };
 
 // Initialisation, observables, reductions and population transfers.

@@ -912,14 +912,14 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
 // ... down to the halo row y1 and collides m ... y1 - 1.  The two groups
 // share their first rows through shared memory, so a tile of R rows pulls
 // R + 2 rows in R / 2 + 1 steps (k_step_smem: R + 2 steps).  Step k: pull,
-// barrier, collide.
-// IND: the groups synchronise separately after step 0 (named barriers of W
-// threads), so that their load and arithmetic phases drift apart instead of
-// alternating in lock step.  Only the rows of step 0 are read by the other
-// group (at its step 1): they get slots of their own, never reused within
-// the tile, and the step-0 barrier is CTA-wide; density slots of step k >= 1
-// then rotate over 4 per group: group * 5 + 1 + ((k - 1) & 3).
-// Without IND: one CTA-wide barrier per step, slot group * 4 + (k & 3).
+// barrier, collide.  After step 0 the groups synchronise separately (named
+// barriers of W threads), so that their load and arithmetic phases drift
+// apart instead of alternating in lock step (measured on the 8192x160
+// capillary, tile 64x18: 41.0 us per step against 43.2 us with one CTA-wide
+// barrier per step).  Only the rows of step 0 are read by the other group (at
+// its step 1): they get density slots of their own, never reused within the
+// tile, and the step-0 barrier is CTA-wide; the slots of steps k >= 1 rotate
+// over 4 per group: group * 5 + 1 + ((k - 1) & 3).
 template <typename S, int W>
 constexpr int kBidirMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 512 / W;   // 64 registers
 
@@ -930,12 +930,12 @@ __device__ __forceinline__ void bar_group(int g) {
     else asm volatile("bar.sync 2, %0;\n" ::"n"(N) : "memory");
 }
 
-template <typename S, int W, bool G, bool IND>
+template <typename S, int W, bool G>
 __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(const RunDesc* __restrict__ runs,
                                                                               const Tile* __restrict__ tiles,
                                                                               int parity) {
     using C = typename Prec<S>::C;
-    constexpr int NS = IND ? 5 : 4;   // density slots per group
+    constexpr int NS = 5;            // density slots per group
     __shared__ C sd[2 * NS][2][W];   // [group * NS + step slot][species][column]
     __shared__ C ps[2][2][18][W];    // [group][step parity][population][column]
 
@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
     const int nsteps = (y1 - y0 + 1) / 2 + 1;                // same for both groups (U has the larger half)
     // row pulled by this group at step k (the last one is the halo row)
     auto row_at = [&](int k) { return grp_d == 0 ? m - 1 - k : m + k; };
-    auto slot = [&](int g, int k) { return IND ? g * NS + (k == 0 ? 0 : 1 + ((k - 1) & 3)) : g * NS + (k & 3); };
+    auto slot = [&](int g, int k) { return g * NS + (k == 0 ? 0 : 1 + ((k - 1) & 3)); };
 
     auto pull = [&](int k, unsigned& smask) {
         const int r = row_at(k);
@@ -990,7 +990,7 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
     for (int k = 0; k < nsteps; ++k) {
         // this group pulls rows 0 .. nrows (the last is its halo row)
         if (k <= nrows) pull(k, sm_cur);
-        if (!IND || k == 0)
+        if (k == 0)
             __syncthreads();
         else
             bar_group<W>(grp_d);

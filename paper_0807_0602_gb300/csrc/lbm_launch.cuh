@@ -6,7 +6,6 @@
 #include <atomic>
 
 #include "lbm_kernels.cuh"
-#include "lbm_packed.cuh"
 #include "lbm_ring.cuh"
 
 namespace sc {
@@ -205,21 +204,14 @@ cudaError_t Step<S, G>::step_tile(int W, int R, const RunDesc* d_runs, const Til
 }
 
 template <typename S, bool G>
-cudaError_t Step<S, G>::step_bidir(int W, bool ind, const RunDesc* d_runs, const Tile* d_tiles, int ntiles,
-                                  int parity, cudaStream_t s) {
+cudaError_t Step<S, G>::step_bidir(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
+                                  cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     switch (W) {
-        case 64:
-            if (ind) k_step_bidir<S, 64, G, true><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
-            else k_step_bidir<S, 64, G, false><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity);
-            break;
+        case 64: k_step_bidir<S, 64, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
         case 128:
-            if constexpr (sizeof(typename Prec<S>::C) == 8) {
-                return cudaErrorInvalidValue;
-            } else {
-                if (ind) k_step_bidir<S, 128, G, true><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
-                else k_step_bidir<S, 128, G, false><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
-            }
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else k_step_bidir<S, 128, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -265,6 +257,18 @@ cudaError_t Step<S, G>::ring_ctas_per_sm(int D, int* out) {
 }
 
 template <typename S, bool G>
+cudaError_t Step<S, G>::bidir_ctas_per_sm(int W, int* out) {
+    *out = 0;
+    switch (W) {
+        case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step_bidir<S, 64, G>, 128, 0);
+        case 128:
+            if constexpr (sizeof(typename Prec<S>::C) == 8) return cudaErrorInvalidValue;
+            else return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_step_bidir<S, 128, G>, 256, 0);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S, bool G>
 cudaError_t Step<S, G>::step_ring(int D, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int* queue,
                                   int grid, int parity, uint32_t* err, cudaStream_t s) {
     if (grid <= 0 || ntiles <= 0) return cudaSuccess;
@@ -274,22 +278,6 @@ cudaError_t Step<S, G>::step_ring(int D, const RunDesc* d_runs, const Tile* d_ti
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&d_runs, (void*)&d_tiles, (void*)&ntiles, (void*)&queue, (void*)&parity, (void*)&err};
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, (size_t)smem, s);
-}
-
-template <typename S, bool G>
-cudaError_t Step<S, G>::step_bidir_sp(int W, const RunDesc* d_runs, const Tile* d_tiles, int ntiles, int parity,
-                                      cudaStream_t s) {
-    if constexpr (sizeof(typename Prec<S>::C) == 8) {
-        return cudaErrorInvalidValue;
-    } else {
-        if (ntiles <= 0) return cudaSuccess;
-        switch (W) {
-            case 64: k_step_bidir_sp<S, 64, G><<<ntiles, 128, 0, s>>>(d_runs, d_tiles, parity); break;
-            case 128: k_step_bidir_sp<S, 128, G><<<ntiles, 256, 0, s>>>(d_runs, d_tiles, parity); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
 }
 
 template <typename S, bool G>

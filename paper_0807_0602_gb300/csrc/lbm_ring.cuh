@@ -32,7 +32,7 @@
 // CTA exits and records ERR_TIMEOUT.
 #pragma once
 
-#include "lbm_packed.cuh"
+#include "lbm_kernels.cuh"
 
 namespace sc {
 
@@ -51,6 +51,20 @@ struct RingGeom {
     static constexpr size_t smem_bytes() {
         return ring_bytes + dens_bytes + 2 * D * sizeof(uint64_t) + D * sizeof(int) + 16;
     }
+};
+
+// ---- packed FP32 arithmetic of a column pair ------------------------------------
+// Each component is rounded as the scalar operation of Ar<float> would round it:
+// sub(a, b) = fma(b, -1, a) (an exact product, one rounding) and the negated
+// products of the force use -G, which RN rounds symmetrically.
+struct P2 {
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+        return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
 };
 
 // Pulled value pairs of the slot: aligned pair (columns e, e + 1 of the
@@ -89,6 +103,22 @@ __device__ __forceinline__ void set_lane(float2& v, int c, float x) {
 }
 
 // Wall sum of Eq. 11 at one node (the same order as node_state).
+__device__ __forceinline__ void wall_sum(unsigned m, float& Wx, float& Wy) {
+    using A = Ar<float>;
+    using Wc = Wt<float>;
+    Wx = 0.f;
+    Wy = 0.f;
+    if (!m) return;
+    if (SOL(m, 0, 1)) Wx = A::add(Wx, Wc::w1);
+    if (SOL(m, 1, 0)) Wy = A::add(Wy, Wc::w1);
+    if (SOL(m, 0, -1)) Wx = A::sub(Wx, Wc::w1);
+    if (SOL(m, -1, 0)) Wy = A::sub(Wy, Wc::w1);
+    if (SOL(m, 1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }
+    if (SOL(m, 1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::add(Wy, Wc::w5); }
+    if (SOL(m, -1, -1)) { Wx = A::sub(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); }
+    if (SOL(m, -1, 1)) { Wx = A::add(Wx, Wc::w5); Wy = A::sub(Wy, Wc::w5); }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }

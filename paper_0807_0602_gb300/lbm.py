@@ -228,8 +228,7 @@ class Lattice:
         variants of include/lbm.h (0 register pull, 1 cp.async stages, 2 TMA
         ring, 3 pipelined, 4 species split, 5 L2 prefetch, 6 shared-memory
         staged, 7 column pair, 8 node tile, 9 bidirectional, 10 persistent
-        ring, 11 bidirectional with independent groups, 12 bidirectional with
-        the species packed)."""
+        ring)."""
         v = [ctypes.c_int() for _ in range(4)]
         L.check(self._lib.lbm_get_schedule(self._h, *[ctypes.byref(x) for x in v]), "lbm_get_schedule")
         return tuple(int(x.value) for x in v)
@@ -237,6 +236,17 @@ class Lattice:
     @schedule.setter
     def schedule(self, s):
         L.check(self._lib.lbm_set_schedule(self._h, int(s[0]), int(s[1]), int(s[2]), int(s[3])), "lbm_set_schedule")
+
+    def tuning(self):
+        """The autotuner's finalists: [((tile_w, tile_h, kernel, depth),
+        ms per step on back-to-back steps), ...]; empty before tuning."""
+        n = ctypes.c_int()
+        L.check(self._lib.lbm_get_tuning(self._h, 0, None, None, ctypes.byref(n)), "lbm_get_tuning")
+        k = n.value
+        sched = (ctypes.c_int * max(1, 4 * k))()
+        ms = (ctypes.c_float * max(1, k))()
+        L.check(self._lib.lbm_get_tuning(self._h, k, sched, ms, ctypes.byref(n)), "lbm_get_tuning")
+        return [(tuple(sched[4 * j:4 * j + 4]), float(ms[j])) for j in range(k)]
 
     # ---- observables ---------------------------------------------------
     def _pair(self, fn, run, device, name):

@@ -147,6 +147,9 @@ def test_null_handles_and_status_strings(lib):
     from paper_0807_0602_gb300 import _lib as L
     assert lib.lbm_step(None, 1) == L.LBM_EINVAL
     assert lib.lbm_time(None) == -1
+    n = ctypes.c_int(7)
+    assert lib.lbm_get_tuning(None, 0, None, None, ctypes.byref(n)) == L.LBM_EINVAL
+    assert lib.lbm_selftest_fp64_rate(None, None) == L.LBM_EINVAL
     lib.lbm_destroy(None)
     for code in range(9):
         assert lib.lbm_error_string(code)
