@@ -59,19 +59,17 @@ KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_spl
 # keyed by (kernel, tile, species): species None for alpha = 4/9, m = 1, else --species
 SPECIES_1_3 = (4.0 / 9.0, 0.8, 1.0, 25.0 / 9.0)
 PROFILES = {
-    (6, (128, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_f32_capillary_8192x160.txt"),
-    (6, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
+    (9, (64, 18), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x18_f32_capillary_8192x160.txt"),
+    (9, (64, 9), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x9_f32_capillary_8192x160.txt"),
     (9, (64, 8), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
-    (9, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x4_f32_capillary_8192x160.txt"),
-    (9, (64, 12), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x12_f32_capillary_8192x160.txt"),
-    (9, (64, 16), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x16_f32_capillary_8192x160.txt"),
-    (6, (256, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile256x4_f32_capillary_8192x160.txt"),
-    (8, (32, 6), None, "f32"): os.path.join(ROOT, "profiles", "k_step_tile_tile32x6_f32_capillary_8192x160.txt"),
+    (6, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
     (10, (128, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_ring_depth4_f32_capillary_8192x160.txt"),
-    (9, (64, 8), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f16s_capillary_8192x160.txt"),
+    (9, (64, 9), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x9_f16s_capillary_8192x160.txt"),
+    (9, (64, 18), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x18_f16s_capillary_8192x160.txt"),
     (6, (128, 4), None, "f64"): os.path.join(ROOT, "profiles", "k_step_smem_tile128x4_f64_capillary_8192x160.txt"),
-    (9, (64, 8), SPECIES_1_3, "f32"): os.path.join(ROOT, "profiles",
-                                                   "k_step_bidir_species_tile64x8_f32_capillary_8192x160.txt"),
+    (9, (64, 8), None, "f64"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f64_capillary_8192x160.txt"),
+    (9, (64, 18), SPECIES_1_3, "f32"): os.path.join(ROOT, "profiles",
+                                                    "k_step_bidir_species_tile64x18_f32_capillary_8192x160.txt"),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
                   for f in ("lbm_kernels.cuh", "lbm_ring.cuh", "lbm_launch.cuh", "kernels_f32.cu",
@@ -379,6 +377,82 @@ def select_schedule(lat, stream, flush, steps: int = 24, log_every: int = 50):
     return {"finalists": rows, "chosen": best["schedule"],
             "rule": "the tuner's finalists re-timed under this line's protocol (L2 flushed before each step); "
                     "the fastest median kept"}
+
+
+def fp64_ops_per_node():
+    """FP64 instructions per node of the step (DADD + DMUL + DFMA thread
+    instructions, from the committed FP64 ncu summary), or None when the
+    kernel sources changed since.  Every FP64 step kernel evaluates the same
+    canonical arithmetic, so the count holds for each of them."""
+    path = PROFILES[(6, (128, 4), None, "f64")]
+    try:
+        kv = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_hash") != kernel_hash():
+            return None
+        return float(kv["fp64_ops_per_node"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measure_precision(stream, dev, precision: str, steps: int = 200):
+    """The headline workload in another storage precision: autotuned, the
+    finalists re-timed under the headline's protocol, then `steps` steps
+    timed one by one after the L2 flush (log every 50 steps, logged steps
+    left out of the kernel time).  Roofline against HBM; FP64 also against
+    the FP64 pipe (its measured rate, lbm_selftest_fp64_rate)."""
+    import ctypes
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_0807_0602_gb300 import _lib as L
+    from paper_0807_0602_gb300.lbm import Lattice
+    c = workload()
+    g = c["geom"]
+    nodes, fluid = g["nx"] * g["ny"], g["nx"] * g["ny"] - 2 * (g["cap_x1"] - g["cap_x0"])
+    shift = W.fp16_shift(dict(geom=g, params=c["params"], init=c["init"])) if precision == "f16s" else (0.0, 0.0)
+    with torch.cuda.stream(stream):
+        lat = Lattice(dict(geom=g, params=c["params"], init=c["init"]), precision=precision, log_every=50,
+                      log_capacity=4096, autotune=True, stream=stream, rho_ref=shift)
+        lat.step(TUNE_STEPS)
+        lat.sync()
+        flush = Flush(dev)
+        selection = select_schedule(lat, stream, flush)
+        durs, t0 = timed_steps(lat, stream, flush, steps)
+        kern = [d for k, d in enumerate(durs) if (t0 + k + 1) % 50 != 0]
+        sched = lat.schedule
+        finite = bool(np.all(np.isfinite(lat.mass())))
+        lat.close()
+    kernel_ms = statistics.mean(kern)
+    peak, peak_kind = peaks()
+    alg = fluid * BYTES_PER_NODE[precision]
+    gbs = alg / (kernel_ms * 1e-3) / 1e9
+    out = {"value": nodes * steps / (sum(durs) * 1e-3) / 1e9, "unit": "GLUPS", "steps": steps,
+           "rho_ref": list(shift), "schedule": {"tile": list(sched[:2]), "kernel": KERNELS[sched[2]]},
+           "schedule_selection": selection, "state_finite": finite,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "traffic": read_traffic(sched[2], sched[:2], precision), "peak_source": peak_kind,
+                        "alg_bytes_per_launch": alg, "kernel_ms": kernel_ms}}
+    if precision == "f64":
+        rate = ctypes.c_double()
+        lib = L.load()
+        with torch.cuda.stream(stream):
+            L.check(lib.lbm_selftest_fp64_rate(ctypes.byref(rate), ctypes.c_void_p(stream.cuda_stream)),
+                    "lbm_selftest_fp64_rate")
+        ops = fp64_ops_per_node()
+        fp64 = {"bound": "fp64 pipe", "unit": "FP64 instructions/s",
+                "peak": rate.value / 2.0, "peak_source": "measured: lbm_selftest_fp64_rate (DFMA chains, "
+                                                         "2 flops each) / 2 = DFMA instructions per second",
+                "ops_per_node": ops}
+        if ops is not None:
+            fp64["achieved"] = nodes * ops / (kernel_ms * 1e-3)
+            fp64["frac"] = fp64["achieved"] / fp64["peak"]
+        out["roofline_fp64"] = fp64
+    return out
 
 
 def measure_density_ratio(stream, dev, precision: str, steps: int = 1000):
@@ -833,6 +907,8 @@ def main():
     physics = (measure_capillary_physics() if (rank == 0 and not args.no_batched) else None)
     density_ratio = (measure_density_ratio(stream, dev, args.precision)
                      if (rank == 0 and not args.no_batched and SPECIES is None) else None)
+    others = ({p: measure_precision(stream, dev, p) for p in ("f16s", "f64") if p != args.precision}
+              if (rank == 0 and not args.no_batched) else None)
     surrogate = measure_surrogate() if (rank == 0 and not args.no_batched) else None
     accuracy = measure_accuracy() if (rank == 0 and not args.no_batched) else None
     if rank != 0:
@@ -868,6 +944,8 @@ def main():
         line["batched"] = batched
         if density_ratio is not None:
             line["density_ratio"] = density_ratio
+        if others:
+            line["precisions"] = others
         line["surrogate"] = surrogate
         line["accuracy"] = accuracy
         line["accuracy"]["ensemble_f32_vs_f64"] = ens_acc
