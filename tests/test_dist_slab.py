@@ -91,6 +91,54 @@ def test_two_gloo_ranks_reproduce_the_undivided_run_bit_for_bit():
     assert np.array_equal(got, want)
 
 
+def _leaving_worker(rank, world, port, q):
+    """Rank 1 leaves between steps (after 3 steps and their exchanges, with
+    nothing in flight); rank 0 steps on and must see its next exchange fail
+    instead of waiting forever."""
+    import sys
+    import time
+    from datetime import timedelta
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=10))
+    from paper_0807_0602_gb300 import slab as SL
+    run, nA, nB = _case()
+    sr = SL.SlabRank(run, nA, nB, factory=OracleColumns)
+    sr.step(3)
+    if rank == 1:
+        q.put((rank, "left", 0.0))
+        q.close()
+        q.join_thread()                  # the message is sent before the process vanishes
+        os._exit(0)                      # no destroy_process_group: the peer just disappears
+    t0 = time.monotonic()
+    try:
+        sr.step(3)
+        q.put((rank, "no error", time.monotonic() - t0))
+    except RuntimeError as e:            # gloo reports the lost peer (closed connection or timeout)
+        q.put((rank, "error: " + str(e).splitlines()[0][:80], time.monotonic() - t0))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_makes_the_next_exchange_fail_not_hang():
+    import sys
+    sys.path.insert(0, ROOT)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 28700 + os.getpid() % 1000
+    procs = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r[0], r[1:]) for r in (q.get(timeout=120) for _ in range(2)))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1][0] == "left"
+    assert res[0][0].startswith("error"), res[0]
+    assert res[0][1] < 60.0
+
+
 @pytest.mark.parametrize("parts", [1, 3, 4])
 def test_slabs_of_one_process_reproduce_the_undivided_run(parts):
     from paper_0807_0602_gb300 import slab as SL
