@@ -261,6 +261,16 @@ def test_autotune_keeps_results():
         b.step(1000)
         assert a.t == b.t == 1120
         assert np.array_equal(a.populations(), b.populations())
+        fin = a.tuning()          # the finalists, each a valid schedule with its time
+        assert 2 <= len(fin) <= 4 and b.tuning() == []
+        assert a.schedule in [f[0] for f in fin]
+        assert all(np.isfinite(ms) and ms > 0 for _, ms in fin)
+        for sched, _ in fin:      # re-selecting a finalist keeps the bits
+            a.schedule = sched
+            b.schedule = sched
+            a.step(3)
+            b.step(3)
+            assert np.array_equal(a.populations(), b.populations())
 
 
 def test_checkpoint_resume_is_bit_identical(tmp_path):
