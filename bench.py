@@ -52,28 +52,36 @@ BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
 # passes of the tuner (about 90 candidates x 7 steps, then 4 x 33)
 TUNE_STEPS = 1200
 KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
-           "node-tile", "bidirectional", "ring"]
+           "node-tile", "bidirectional", "ring", "bidirectional-jit"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",
-                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir", "k_step_ring"]
+                "k_step_smem", "k_step_pair", "k_step_tile", "k_step_bidir", "k_step_ring",
+                "k_step_bidir (compiled for the grid)"]
 # committed ncu summaries of the step kernel on this workload, by (variant, tile)
 # keyed by (kernel, tile, species): species None for alpha = 4/9, m = 1, else --species
 SPECIES_1_3 = (4.0 / 9.0, 0.8, 1.0, 25.0 / 9.0)
 PROFILES = {
+    (11, (64, 18), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_jit_tile64x18_f32_capillary_8192x160.txt"),
+    (11, (64, 9), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_jit_tile64x9_f32_capillary_8192x160.txt"),
     (9, (64, 18), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x18_f32_capillary_8192x160.txt"),
     (9, (64, 9), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x9_f32_capillary_8192x160.txt"),
-    (9, (64, 8), None, "f32"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f32_capillary_8192x160.txt"),
     (6, (64, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_smem_tile64x4_f32_capillary_8192x160.txt"),
     (10, (128, 4), None, "f32"): os.path.join(ROOT, "profiles", "k_step_ring_depth4_f32_capillary_8192x160.txt"),
+    (11, (64, 9), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_jit_tile64x9_f16s_capillary_8192x160.txt"),
+    (11, (64, 18), None, "f16s"): os.path.join(ROOT, "profiles",
+                                               "k_step_bidir_jit_tile64x18_f16s_capillary_8192x160.txt"),
     (9, (64, 9), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x9_f16s_capillary_8192x160.txt"),
-    (9, (64, 18), None, "f16s"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x18_f16s_capillary_8192x160.txt"),
     (6, (128, 4), None, "f64"): os.path.join(ROOT, "profiles", "k_step_smem_tile128x4_f64_capillary_8192x160.txt"),
-    (9, (64, 8), None, "f64"): os.path.join(ROOT, "profiles", "k_step_bidir_tile64x8_f64_capillary_8192x160.txt"),
+    (0, (128, 4), None, "f64"): os.path.join(ROOT, "profiles",
+                                             "k_step_register_tile128x4_f64_capillary_8192x160.txt"),
+    (11, (64, 8), None, "f64"): os.path.join(ROOT, "profiles", "k_step_bidir_jit_tile64x8_f64_capillary_8192x160.txt"),
     (9, (64, 18), SPECIES_1_3, "f32"): os.path.join(ROOT, "profiles",
                                                     "k_step_bidir_species_tile64x18_f32_capillary_8192x160.txt"),
+    (11, (64, 18), SPECIES_1_3, "f32"): os.path.join(ROOT, "profiles",
+                                                     "k_step_bidir_jit_species_tile64x18_f32_capillary_8192x160.txt"),
 }
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0807_0602_gb300", "csrc", f)
                   for f in ("lbm_kernels.cuh", "lbm_ring.cuh", "lbm_launch.cuh", "kernels_f32.cu",
-                            "kernels_gen_f32.cu", "lbm_device.h")]
+                            "kernels_gen_f32.cu", "lbm_device.h", "lbm_jit.cu")]
 
 
 # (alpha_A, alpha_B, m_A, m_B) of --species, or None for alpha = 4/9, m = 1

@@ -44,8 +44,21 @@
 #ifndef SHANCHEN_GB300_LBM_H
 #define SHANCHEN_GB300_LBM_H
 
+#ifdef __CUDACC_RTC__
+/* run-time compilation of the step kernel (NVRTC has no C library headers) */
+typedef decltype(sizeof(0)) size_t;
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -328,7 +341,15 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         segments of the strips from a device counter.
  *                         LBM_F32 and LBM_F16S only; tile_w must be 128 (the
  *                         segment height is chosen by the library, tile_h is
- *                         only recorded); nx >= 4.
+ *                         only recorded); nx >= 4;
+ *   LBM_KERNEL_BIDIR_JIT  LBM_KERNEL_BIDIR compiled by NVRTC when the
+ *                         schedule is set, with the run's nx, ny, pitch and
+ *                         plane as constants, so that every load and store
+ *                         addresses its plane and row by an immediate offset
+ *                         (same tilings as LBM_KERNEL_BIDIR; handles of one
+ *                         run only).  The compiled kernel is cached for the
+ *                         process; setting the schedule returns LBM_ECUDA if
+ *                         the run-time compiler or the module load fails.
  * depth is read by LBM_KERNEL_ASYNC, LBM_KERNEL_TMA and LBM_KERNEL_RING and
  * must be 4 for the others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */
@@ -344,6 +365,7 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
                                     (W = 64: R in {6, 14}); nx >= 4 */
 #define LBM_KERNEL_BIDIR 9       /* two thread groups marching away from the tile's middle row */
 #define LBM_KERNEL_RING 10       /* persistent producer/consumer ring of bulk-copied row slots (FP32, FP16S) */
+#define LBM_KERNEL_BIDIR_JIT 11  /* LBM_KERNEL_BIDIR compiled at run time for the handle's grid (one run) */
 int lbm_get_schedule(const lbm_t* h, int* tile_w, int* tile_h, int* kernel, int* depth);
 /* The autotuner's finalists (the paper has no counterpart: this reports on the
  * library's own schedule search).  *count = number of finalists (0 before

@@ -36,7 +36,11 @@ UNITS = {
     "mlp.cu": [],
     "lbm_noalloc.cu": [],
     "lbm_selftest.cu": [],
+    "lbm_jit.cu": [],
 }
+# headers that the run-time compiled step kernel includes (embedded into the
+# library by write_jit_sources, in this order)
+JIT_HEADERS = [os.path.join(INCLUDE, "lbm.h"), os.path.join(CSRC, "lbm_device.h"), os.path.join(CSRC, "lbm_kernels.cuh")]
 
 
 def _nvcc() -> str:
@@ -49,6 +53,29 @@ def _nvcc() -> str:
 def _sources():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + [
         os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+
+
+def write_jit_sources(build_dir: str, nvcc: str) -> None:
+    """Writes lbm_jit_sources.h: the step kernel's headers as string literals
+    and the toolkit's include directory (for cuda_fp16.h), for NVRTC."""
+    inc = os.path.realpath(os.path.join(os.path.dirname(os.path.realpath(nvcc)), "..", "include"))
+    lines = ["// Written by build.py: the headers of the run-time compiled step kernel.", "#pragma once",
+             f'#define LBM_CUDA_INCLUDE "{inc}"', f"static const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "static const char* const kJitHeaderNames[] = {" +
+             ", ".join(f'"{os.path.basename(h)}"' for h in JIT_HEADERS) + "};",
+             "static const char* const kJitHeaders[] = {"]
+    for h in JIT_HEADERS:
+        with open(h) as fh:
+            text = fh.read()
+        if ")LBMJIT\"" in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        lines.append('R"LBMJIT(' + text + ')LBMJIT",')
+    lines.append("};")
+    path = os.path.join(build_dir, "lbm_jit_sources.h")
+    new = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != new:
+        with open(path, "w") as fh:
+            fh.write(new)
 
 
 def up_to_date(lib: str = LIB) -> bool:
@@ -67,6 +94,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         return lib_path
     os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
+    write_jit_sources(build_dir, nvcc)
     procs = []
     objs = []
     for unit, extra in UNITS.items():
@@ -74,7 +102,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         if not os.path.exists(src):
             continue
         obj = os.path.join(build_dir, unit.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *COMMON, *defines, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *COMMON, "-I" + build_dir, *defines, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((unit, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -87,7 +115,8 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = lib_path + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    libdir = os.path.realpath(os.path.join(os.path.dirname(os.path.realpath(nvcc)), "..", "lib64"))
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker", "-rpath", "-Xlinker", libdir]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

@@ -11,6 +11,7 @@
 
 #include "lbm.h"
 #include "lbm_device.h"
+#include "lbm_jit.h"
 
 using sc::RunDesc;
 using sc::Tile;
@@ -53,9 +54,11 @@ struct lbm_s {
                                    // pull with the pulled rows parked in shared memory, 7 two columns per
                                    // thread, 8 one node per thread over a W x (R + 2) tile, 9 two thread
                                    // groups marching away from the tile's middle row, 10 persistent
-                                   // producer/consumer ring of row slots filled by bulk copies
+                                   // producer/consumer ring of row slots filled by bulk copies, 11 the
+                                   // bidirectional march compiled at run time for the run's grid
     int* d_queue = nullptr;        // ring kernel: segment counter and finished-CTA counter
     int ring_grid = 0;             // ring kernel: CTAs of the persistent grid
+    const void* jit_fn = nullptr;  // kvar 11: the bidirectional march compiled for this run's grid
     std::vector<int2> rows;
     int2* d_rows = nullptr;
     double* d_partials = nullptr;
@@ -265,6 +268,13 @@ int upload_tiles(lbm_t* h, int W, int R) {
             CK(h, cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(int), h->stream));
         }
     } else {
+        if (h->kvar == 11) {
+            const RunDesc& rd = h->runs[0];
+            const void* fn = nullptr;
+            const int rc = sc::jit_bidir(h->precision, W, h->gen != 0, rd.nx, rd.ny, rd.pitch, rd.plane, &fn);
+            if (rc) return rc;
+            h->jit_fn = fn;
+        }
         build_tiles(h, W, R);
     }
     const size_t need = h->tiles.size() * sizeof(Tile);
@@ -321,11 +331,23 @@ cudaError_t issue_step(lbm_t* h, int parity, cudaStream_t s) {
         return dispatch_step(h, [&](auto L) {
             return L.step_ring(h->depth, h->d_runs, h->d_tiles, nt, h->d_queue, h->ring_grid, parity, h->d_err, s);
         });
+    if (h->kvar == 11) {
+        if (nt <= 0) return cudaSuccess;
+        const RunDesc* runs = h->d_runs;
+        const Tile* tiles = h->d_tiles;
+        int par = parity;
+        void* args[] = {&runs, &tiles, &par};
+        return cudaLaunchKernel(h->jit_fn, dim3(nt), dim3(2 * W), args, 0, s);
+    }
     return dispatch_step(h, [&](auto L) { return L.step(W, h->d_runs, h->d_tiles, nt, parity, s); });
 }
 
 bool schedule_ok(const lbm_t* h, int W, int R, int kvar, int depth) {
-    if (R < 1 || kvar < 0 || kvar > 10) return false;
+    if (R < 1 || kvar < 0 || kvar > 11) return false;
+    if (kvar == 11) {   // the bidirectional march compiled for the grid: one run per handle
+        if (h->nruns != 1) return false;
+        kvar = 9;
+    }
     if (kvar == 10) {
         // ring of `depth` row slots (3, 4 or 5) fed by bulk copies: FP32 and
         // FP16S storage; strips of 120 columns (tile_w 128; the segment height
@@ -520,6 +542,21 @@ int autotune(lbm_t* h, int64_t* n) {
             const int R = wave_height(h, W, waves);
             if (R > 0 && std::find(Rs.begin(), Rs.end(), R) == Rs.end() && schedule_ok(h, W, R, 9, 4))
                 cands.push_back({W, R, 9, 4});
+        }
+    }
+    // a single run: the bidirectional march compiled for its grid, at the
+    // wave-filling heights (only where the run-time compiler is available)
+    if (h->nruns == 1) {
+        const RunDesc& rd = h->runs[0];
+        for (int W : {64, 128}) {
+            const void* fn = nullptr;
+            if (!schedule_ok(h, W, 4, 11, 4) ||
+                sc::jit_bidir(h->precision, W, h->gen, rd.nx, rd.ny, rd.pitch, rd.plane, &fn) != LBM_OK)
+                continue;
+            for (int waves : {1, 2}) {
+                const int R = wave_height(h, W, waves);
+                if (R > 0) cands.push_back({W, R, 11, 4});
+            }
         }
     }
     for (int W : {32, 64})

@@ -5,8 +5,10 @@
 #include <cuda_fp16.h>
 
 #include "lbm.h"
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace sc {
 
@@ -51,6 +53,7 @@ struct RunDesc {
 // Fills rd.c32 from the FP64 fields (round to nearest, as a device conversion
 // would).  The FP16S shift stays w_g rho_ref for every alpha_k: it is only the
 // offset of the stored values, the same in the step and in the mass sums.
+#ifndef __CUDACC_RTC__
 inline void fill_coef_f32(RunDesc& rd) {
     CoefF32& c = rd.c32;
     c.G = (float)rd.G;
@@ -73,6 +76,7 @@ inline void fill_coef_f32(RunDesc& rd) {
             c.sh[k][g] = w[g] * (float)rd.rho_ref[k];
         }
 }
+#endif
 
 // column chunks (CTAs) per row of the mass reduction
 constexpr int kMassChunks = 4;
@@ -106,6 +110,7 @@ struct LogCtl {
 
 enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u, ERR_BOUNDS = 4u };   // ERR_BOUNDS: checked builds
 
+#ifndef __CUDACC_RTC__   // host launchers: not part of a run-time compiled step kernel
 // Step kernels (one pass of Eq. 2 over every tile) and the moments pass.
 // GEN: the runs have some alpha_k != 4/9 or m_k != 1.
 template <typename S, bool GEN>
@@ -176,5 +181,6 @@ extern template struct Step<float, false>;
 extern template struct Step<float, true>;
 extern template struct Step<__half, false>;
 extern template struct Step<__half, true>;
+#endif
 
 }  // namespace sc

@@ -942,8 +942,20 @@ __global__ void __launch_bounds__(2 * W, (kBidirMinBlocks<S, W>)) k_step_bidir(c
     const Tile tl = tiles[blockIdx.x];
     const RunDesc& rd = runs[tl.run];
     if (!step_tile_ok(tl, rd)) return;
+#ifdef LBM_JIT_GRID
+    // compiled at run time for one grid (LBM_KERNEL_BIDIR_JIT): its sizes are
+    // constants, so the plane and row offsets of the 18 loads and 18 stores
+    // fold into the instructions' immediates; a run of another size is refused
+    constexpr int nx = LBM_JIT_NX, ny = LBM_JIT_NY, pitch = LBM_JIT_PITCH;
+    constexpr unsigned plane = LBM_JIT_PLANE;
+    if (rd.nx != nx || rd.ny != ny || rd.pitch != pitch || rd.plane != (long long)plane) {
+        if (threadIdx.x == 0 && rd.err) atomicOr(rd.err, ERR_BOUNDS);
+        return;
+    }
+#else
     const int nx = rd.nx, ny = rd.ny, pitch = rd.pitch;
     const unsigned plane = (unsigned)rd.plane;
+#endif
     const Geo geo{nx, rd.cap_x0, rd.cap_x1, rd.y_bot, rd.y_top, rd.mask};
     const S* __restrict__ src = static_cast<const S*>(rd.buf[parity]);
     S* __restrict__ dst = static_cast<S*>(rd.buf[parity ^ 1]);

@@ -228,7 +228,7 @@ class Lattice:
         variants of include/lbm.h (0 register pull, 1 cp.async stages, 2 TMA
         ring, 3 pipelined, 4 species split, 5 L2 prefetch, 6 shared-memory
         staged, 7 column pair, 8 node tile, 9 bidirectional, 10 persistent
-        ring)."""
+        ring, 11 bidirectional compiled at run time for the run's grid)."""
         v = [ctypes.c_int() for _ in range(4)]
         L.check(self._lib.lbm_get_schedule(self._h, *[ctypes.byref(x) for x in v]), "lbm_get_schedule")
         return tuple(int(x.value) for x in v)

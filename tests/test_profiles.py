@@ -28,8 +28,8 @@ def test_bench_profile_table_points_at_matching_summaries():
         assert int(kv["dram_bytes_per_launch"]) > 0
         assert len(kv["kernel_hash"]) == 16
         name = os.path.basename(path)
-        assert name.startswith({2: "k_step_tma", 6: "k_step_smem", 8: "k_step_tile", 9: "k_step_bidir",
-                                10: "k_step_ring"}[kvar]), name
+        assert name.startswith({0: "k_step_register", 2: "k_step_tma", 6: "k_step_smem", 8: "k_step_tile",
+                                9: "k_step_bidir", 10: "k_step_ring", 11: "k_step_bidir_jit"}[kvar]), name
         assert ("species" in name) == (species is not None), name
         assert f"_{precision}_" in name, name
 
