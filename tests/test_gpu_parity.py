@@ -257,9 +257,9 @@ def test_autotune_keeps_results():
         a.step(120)               # too few steps to time every candidate: no tuning yet
         b.step(120)
         assert a.schedule == b.schedule
-        a.step(1000)              # both passes of the tuner run on these real steps
-        b.step(1000)
-        assert a.t == b.t == 1120
+        a.step(1500)              # both passes of the tuner run on these real steps
+        b.step(1500)
+        assert a.t == b.t == 1620
         assert np.array_equal(a.populations(), b.populations())
         fin = a.tuning()          # the finalists, each a valid schedule with its time
         assert 2 <= len(fin) <= 4 and b.tuning() == []
