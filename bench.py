@@ -779,13 +779,24 @@ def run_profile(args):
     build_lib()
     c = workload()
     w, h, k, d = (int(v) for v in args.schedule.split(","))
-    # the z(t) and mass log every 50 steps as in the timed run
-    with Lattice(dict(geom=c["geom"], params=c["params"], init=c["init"]), precision=args.precision, tile=(w, h),
-                 kernel=(k, d), graph_chunk=-1, log_every=50, log_capacity=4096) as lat:
+    if args.ensemble:
+        # the first runs of the uneven ensemble (a few GB, for ncu); the
+        # coupling does not change the kernel's work, so it is fixed here
+        import workloads as W
+        runs = W.batch_uneven_capillaries_stable(512, seed=3)[:args.ensemble]
+        for r in runs:
+            r["params"]["G_Aw"] = -0.2
+        what = runs
+    else:
+        # the z(t) and mass log every 50 steps as in the timed run
+        what = dict(geom=c["geom"], params=c["params"], init=c["init"])
+    with Lattice(what, precision=args.precision, tile=(w, h), kernel=(k, d), graph_chunk=-1,
+                 log_every=0 if args.ensemble else 50, log_capacity=4096) as lat:
         lat.step(args.profile)
         lat.sync()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_steps": args.profile, "schedule": [w, h, k, d], "precision": args.precision}))
+    print(json.dumps({"profile_steps": args.profile, "schedule": [w, h, k, d], "precision": args.precision,
+                      "ensemble_runs": args.ensemble}))
     return 0
 
 
@@ -802,6 +813,8 @@ def main():
                     help="only step the workload this many times (for ncu captures) and exit")
     ap.add_argument("--schedule", default="128,4,6,4",
                     help="tile_w,tile_h,kernel,depth used by --profile")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="with --profile: step the first this many runs of the uneven ensemble instead")
     ap.add_argument("--species", default=None,
                     help="alpha_A,alpha_B,m_A,m_B: rest fractions (Eqs. 3-5) and molecular masses of the species")
     args = ap.parse_args()
