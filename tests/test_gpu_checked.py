@@ -1,6 +1,7 @@
 """The checked build (-DLBM_CHECKED) on valid inputs: every step kernel and
 the mass sums validate their tiles and rows first, find nothing outside the
-run's buffers, and give the same bits as the default build.
+run's buffers, and give the same bits as the default build (the kernel
+compiled at run time for the grid is compiled with the same checks).
 
 The checked library is loaded in a child process (LBM_CHECKED=1), so this
 process keeps the default build.
@@ -25,7 +26,7 @@ from paper_0807_0602_gb300.lbm import Lattice
 assert L.load()._name.endswith("_checked.so"), L.load()._name
 SCHEDULES = [(None, None), ((128, 16), (0, 4)), ((64, 3), (1, 4)), ((64, 7), (2, 4)), ((64, 5), (3, 4)),
              ((128, 16), (4, 4)), ((128, 9), (5, 4)), ((64, 4), (6, 4)), ((64, 6), (7, 4)), ((32, 6), (8, 4)),
-             ((64, 8), (9, 4))]
+             ((64, 8), (9, 4)), ((64, 5), (11, 4))]
 cases = [(W.capillary_geometry(17, 9, 3, 14, 1, 7), W.params(1.1, 1.2, 0.8, 0.1, -0.1)),
          (W.capillary_geometry(300, 5, 0, 300, 0, 4), W.params(1.0, 1.0, 1.0, -0.1, 0.1)),
          (W.periodic_box(5, 4), dict(W.params(0.9, 1.0, 1.0), alpha=(4 / 9, 0.8), mass=(1.0, 2.0)))]
