@@ -349,7 +349,8 @@ int lbm_set_tiling(lbm_t* h, int tile_w, int tile_h);
  *                         (same tilings as LBM_KERNEL_BIDIR; handles of one
  *                         run only).  The compiled kernel is cached for the
  *                         process; setting the schedule returns LBM_ECUDA if
- *                         the run-time compiler or the module load fails.
+ *                         the run-time compiler or the module load fails,
+ *                         and the handle then keeps its previous schedule.
  * depth is read by LBM_KERNEL_ASYNC, LBM_KERNEL_TMA and LBM_KERNEL_RING and
  * must be 4 for the others.  lbm_set_schedule returns LBM_EINVAL for an unsupported
  * combination, leaving the schedule unchanged. */

@@ -1108,6 +1108,12 @@ int lbm_get_tuning(const lbm_t* h, int max, int* sched, float* ms_per_step, int*
 
 int lbm_set_schedule(lbm_t* h, int tile_w, int tile_h, int kernel, int depth) {
     if (!h || !schedule_ok(h, tile_w, tile_h, kernel, depth)) return LBM_EINVAL;
+    if (kernel == 11) {   // compile first: if that fails, the handle keeps its schedule
+        const RunDesc& rd = h->runs[0];
+        const void* fn = nullptr;
+        const int rc = sc::jit_bidir(h->precision, tile_w, h->gen, rd.nx, rd.ny, rd.pitch, rd.plane, &fn);
+        if (rc) return rc;
+    }
     h->tuned = true;
     h->kvar = kernel;
     h->depth = depth;
