@@ -58,8 +58,10 @@ def capillary_prefactor(run_log, L_cap, mu_l, mu_g, t_min):
     """Washburn prefactor gamma H cos(theta) / (3 mu_l) from a front log:
     twice the slope of Eq. 15's viscous law F(z) against t over mu_l."""
     t, z = run_log[:, 0], run_log[:, 1]
+    if not np.all(np.isfinite(z[t >= t_min])):    # a run that diverged has no prefactor
+        return float("nan")
     m = (t >= t_min) & (z > 0) & (z < 0.9 * L_cap)
-    if m.sum() < 3 or not np.all(np.isfinite(z[m])):
+    if m.sum() < 3:
         return float("nan")
     F = mu_g * L_cap * z[m] + 0.5 * (mu_l - mu_g) * z[m] ** 2
     return 2.0 * float(np.polyfit(t[m], F, 1)[0]) / mu_l

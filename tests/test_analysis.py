@@ -54,3 +54,26 @@ def test_droplet_angle_of_a_constructed_cap(theta):
     nA[0], nB[0] = 0.0, 0.0
     ang, circ = A.droplet_contact_angle(nA, nB, wall_y=0.5, skip_rows=3)
     assert ang == pytest.approx(theta, abs=1.0)
+
+
+@pytest.mark.parametrize("mu_l,mu_g", [(0.4, 1.05), (1.1, 0.43), (0.5, 0.5)])
+def test_campaign_prefactor_recovers_the_viscous_law_of_eq15(mu_l, mu_g):
+    """The surrogate campaign's Washburn prefactor fit: a front that follows
+    Eq. 15's viscous law exactly, (mu_l - mu_g)(z^2 - z0^2)/2 + mu_g L (z - z0)
+    = D t with D = gamma H cos(theta) / 6, plus a start-up lag that shifts t,
+    gives back 2 D / mu_l (the Washburn prefactor gamma H cos(theta) / (3 mu_l)),
+    whatever the viscosity ratio; records past 0.9 L are left out."""
+    from paper_0807_0602_gb300.campaign import capillary_prefactor
+    L, z0, D, lag = 2048.0, 400.0, 0.9, 700.0
+    t = np.arange(0.0, 60000.0, 500.0)
+    a = 0.5 * (mu_l - mu_g)
+    b = mu_g * L
+    c = -(a * z0 ** 2 + b * z0 + D * np.maximum(t - lag, 0.0))
+    z = (-b + np.sqrt(b * b - 4 * a * c)) / (2 * a) if a != 0 else -c / b
+    z = np.minimum(z, 0.95 * L)                   # a filled capillary stops at its end
+    log = np.column_stack([t, z, z + 5.0, z + 5.0, np.ones_like(t), np.ones_like(t)])
+    got = capillary_prefactor(log, L, mu_l, mu_g, t_min=2000.0)
+    assert abs(got - 2.0 * D / mu_l) <= 1e-9 * (2.0 * D / mu_l)
+    bad = log.copy()
+    bad[10, 1] = np.nan                           # a diverged run gives no prefactor
+    assert math.isnan(capillary_prefactor(bad, L, mu_l, mu_g, t_min=2000.0))
