@@ -311,8 +311,10 @@ def measure_ensemble_accuracy(runs, n_runs: int = 64, steps: int = 20000, log_ev
         L = run["geom"]["cap_x1"] - run["geom"]["cap_x0"]
         mu_l, mu_g = 2.04 * (p["tau_A"] - 0.5) / 3.0, 2.04 * (p["tau_B"] - 0.5) / 3.0
         t, z = lg[:, 0], lg[:, 1]
+        if not np.all(np.isfinite(z[t >= steps / 4])):    # a diverged run has no prefactor
+            return float("nan")
         m = (t >= steps / 4) & (z > 0) & (z < 0.9 * L)
-        if m.sum() < 3 or not np.all(np.isfinite(z[m])):
+        if m.sum() < 3:
             return float("nan")
         F = mu_g * L * z[m] + 0.5 * (mu_l - mu_g) * z[m] ** 2
         return float(np.polyfit(t[m], F, 1)[0])
@@ -322,12 +324,13 @@ def measure_ensemble_accuracy(runs, n_runs: int = 64, steps: int = 20000, log_ev
         a, b = slope(run, logs["f64"][r]), slope(run, logs["f32"][r])
         if np.isfinite(a) and abs(a) > 1e-12 and np.isfinite(b):
             rel.append(abs(b - a) / abs(a))
-        dz.append(float(np.nanmax(np.abs(logs["f32"][r][:, 1:4] - logs["f64"][r][:, 1:4]))))
+        dz.append(float(np.max(np.abs(logs["f32"][r][:, 1:4] - logs["f64"][r][:, 1:4]))))   # NaN if not finite
     rel = np.array(rel)
     return {"runs": len(sub), "steps": steps, "prefactor_runs_fitted": int(len(rel)),
             "prefactor_rel_err_max": float(rel.max()) if len(rel) else None,
             "prefactor_rel_err_median": float(np.median(rel)) if len(rel) else None,
             "front_err_lu_max": float(np.nanmax(dz)), "front_err_lu_median": float(np.nanmedian(dz)),
+            "runs_not_finite": int(np.sum(~np.isfinite(dz))),
             "selection": f"the {n_runs} runs with the fewest nodes of the 512-run ensemble"}
 
 
