@@ -77,3 +77,22 @@ def test_campaign_prefactor_recovers_the_viscous_law_of_eq15(mu_l, mu_g):
     bad = log.copy()
     bad[10, 1] = np.nan                           # a diverged run gives no prefactor
     assert math.isnan(capillary_prefactor(bad, L, mu_l, mu_g, t_min=2000.0))
+
+
+def test_coupling_for_angle_inverts_a_table_that_is_bilinear_in_g_and_tau_and_linear_in_the_coupling():
+    """The calibration-table inversion used to map target angles to wall
+    couplings: with theta(G, tau_B, G_Aw) = 80 + 40 G_Aw + 10 (G - 1) - 8 (tau_B - 1)
+    (bilinear in G, tau_B and linear in the coupling, so interpolation is
+    exact), a target angle anywhere inside the grid comes back as the exact
+    coupling; angles beyond the table's range give its end couplings."""
+    from paper_0807_0602_gb300.calibrate import coupling_for_angle
+    Gs, taus, cps = np.array([1.0, 1.05, 1.1]), np.array([1.0, 1.25, 1.5]), np.linspace(-0.5, 0.3, 9)
+    th = lambda G, t, a: 80.0 + 40.0 * a + 10.0 * (G - 1.0) - 8.0 * (t - 1.0)   # noqa: E731
+    table = np.array([[[th(G, t, a) for a in cps] for t in taus] for G in Gs])
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        G, t, a = rng.uniform(1.0, 1.1), rng.uniform(1.0, 1.5), rng.uniform(-0.5, 0.3)
+        got = coupling_for_angle(table, Gs, taus, cps, G, t, th(G, t, a))
+        assert abs(got - a) < 1e-12
+    assert coupling_for_angle(table, Gs, taus, cps, 1.05, 1.2, 10.0) == -0.5
+    assert coupling_for_angle(table, Gs, taus, cps, 1.05, 1.2, 170.0) == 0.3
