@@ -526,6 +526,7 @@ int autotune(lbm_t* h, int64_t* n) {
     for (auto& rd : h->runs) maxny = std::max(maxny, rd.ny);
     std::vector<int> Rs = {4, 8, 16, 32};
     if (maxny < 32) Rs.push_back(maxny);
+    if (maxny >= 96) Rs.push_back(64);   // tall tiles: the TMA ring fills each tile's slots once
     std::sort(Rs.begin(), Rs.end());
     Rs.erase(std::unique(Rs.begin(), Rs.end()), Rs.end());
     // the variants that have been competitive somewhere; the cp.async and
