@@ -49,8 +49,9 @@ WORKLOAD = ("binary Shan-Chen D2Q9 capillary 8192x160, L_cap 6144, H 128, FP32 p
             "G 1.4, tau_A = tau_B = 1, complete-wetting wall, z(t) + mass log every 50 steps")
 BYTES_PER_NODE = {"f64": 288, "f32": 144, "f16s": 72}
 # steps of the first lbm_step call of an autotuned handle: enough for both
-# passes of the tuner (about 95 candidates x 7 steps, then 3 rounds of 4 x 33)
-TUNE_STEPS = 1500
+# passes of the tuner (up to about 120 candidates x 7 steps, then 3 rounds of
+# 4 x 33)
+TUNE_STEPS = 2000
 KERNELS = ["register", "cp.async", "tma", "pipelined", "split", "l2-prefetch", "smem-staged", "column-pair",
            "node-tile", "bidirectional", "ring", "bidirectional-jit"]
 KERNEL_NAMES = ["k_step", "k_step_async", "k_step_tma", "k_step_pf", "k_step_split", "k_step (L2 prefetch)",

@@ -128,7 +128,7 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  * log_capacity  records kept per run (a ring: the newest log_capacity).
  * autotune      1 = time the candidate tilings during the first lbm_step
  *               call long enough for them (every candidate for 6 steps,
- *               the 4 fastest again in 3 rounds of 32; about 1100 steps
+ *               the 4 fastest again in 3 rounds of 32; about 1250 steps
  *               on a large grid) and keep the fastest.  The candidates include, for
  *               the bidirectional march, the tile heights whose tiles fill
  *               one or two waves of resident CTAs.  These are real steps:
