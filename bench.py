@@ -36,6 +36,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -97,11 +98,19 @@ def workload(tau_B: float = 1.0):
     return c
 
 
+def _code(text: str) -> str:
+    """Source text without its comments and blank lines: the hash follows
+    the code that is compiled, not the comments around it."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.strip() for line in text.splitlines() if line.strip())
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

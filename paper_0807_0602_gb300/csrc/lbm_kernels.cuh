@@ -917,9 +917,12 @@ __global__ void __launch_bounds__(W, (kSmemMinBlocks<S, W>)) k_step_smem(const R
 // apart instead of alternating in lock step (measured on the 8192x160
 // capillary, tile 64x18: 41.0 us per step against 43.2 us with one CTA-wide
 // barrier per step).  Only the rows of step 0 are read by the other group (at
-// its step 1): they get density slots of their own, never reused within the
-// tile, and the step-0 barrier is CTA-wide; the slots of steps k >= 1 rotate
-// over 4 per group: group * 5 + 1 + ((k - 1) & 3).
+// its step 1), after the CTA-wide barrier of step 0.  FP64 gives them density
+// slots of their own, never reused within the tile (the slots of steps k >= 1
+// rotate over 4 per group: group * 5 + 1 + ((k - 1) & 3)); FP32 and FP16S
+// rotate all steps over 4 slots per group (group * 4 + (k & 3)) and make the
+// barrier of step 2 CTA-wide too, so that no group reuses its step-0 slot (at
+// step 4) before the other group has read it.
 template <typename S, int W>
 constexpr int kBidirMinBlocks = sizeof(typename Prec<S>::C) == 8 ? 1 : 512 / W;   // 64 registers
 
