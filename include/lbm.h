@@ -129,11 +129,14 @@ typedef void (*lbm_free_fn)(void* ctx, void* ptr, size_t bytes, void* stream);
  * autotune      1 = time the candidate tilings during the first lbm_step
  *               call long enough for them (every candidate for 6 steps,
  *               the 4 fastest again in 3 rounds of 32; about 1250 steps
- *               on a large grid) and keep the fastest.  The candidates include, for
- *               the bidirectional march, the tile heights whose tiles fill
- *               one or two waves of resident CTAs.  These are real steps:
- *               tilings change only the schedule, and results are
- *               bit-identical for every tiling.
+ *               on a large grid) and keep the fastest.  The candidates
+ *               include, for the bidirectional march, the tile heights whose
+ *               tiles fill one or two waves of resident CTAs, and for a
+ *               handle of one run LBM_KERNEL_BIDIR_JIT at those heights
+ *               (compiled once per grid and strip width, about 0.5 s each,
+ *               where NVRTC is available; left out otherwise).  These are
+ *               real steps: tilings change only the schedule, and results
+ *               are bit-identical for every tiling.
  * tile_w        CTA width (64, 128 or 256 threads; 0 = default 128);
  * tile_h        rows marched per CTA (0 = default 4, clamped to ny).
  *               The step kernel starts as LBM_KERNEL_SMEM where it takes the
