@@ -134,15 +134,22 @@ def capillary_prefactors(samples, L_cap=256, steps=20000, log_every=100, precisi
     return kw, ap
 
 
-def sample_parameters(n, seed, G=(1.0, 1.08), gA=(-0.6, 0.3), gB=(-0.3, 0.5), H=(16, 48)):
+def sample_parameters(n, seed, G=(1.0, 1.08), gA=(-0.6, 0.3), gB=(-0.3, 0.5), H=(16, 48), both=None):
     """Seeded draws of (G_Aw, G_Bw, G, tau_A, tau_B, H) inside the stable band
     of the velocity-shift scheme (tau_A = tau_B = 1); half the samples vary
-    G_Aw with G_Bw = 0 and half the reverse (the paper's two wetting schemes)."""
+    G_Aw with G_Bw = 0 and half the reverse (the paper's two wetting schemes).
+    With both = (G_Aw, (lo, hi)) a third of the samples instead combine the
+    two schemes: G_Aw fixed, G_Bw ~ U[lo, hi] (the strongly wetting angles
+    that neither scheme reaches alone in the stable band)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     X = np.zeros((n, 6))
-    half = n // 2
-    X[:half, 0] = rng.uniform(*gA, size=half)
-    X[half:, 1] = rng.uniform(*gB, size=n - half)
+    nA = n // 3 if both else n // 2
+    nB = n // 3 if both else n - nA
+    X[:nA, 0] = rng.uniform(*gA, size=nA)
+    X[nA:nA + nB, 1] = rng.uniform(*gB, size=nB)
+    if both:
+        X[nA + nB:, 0] = both[0]
+        X[nA + nB:, 1] = rng.uniform(*both[1], size=n - nA - nB)
     X[:, 2] = rng.uniform(*G, size=n)
     X[:, 3] = 1.0
     X[:, 4] = 1.0
@@ -165,11 +172,15 @@ def build_dataset(n, seed, droplet_steps=8000, capillary_steps=20000, L_cap=256,
     return X[ok], T[ok]
 
 
-def bisection(targets_deg, fixed, lo=-0.6, hi=0.3, tol_deg=2.0, max_iter=12, precision="f64", steps=8000):
-    """Plain lattice-model search: bisection on G_Aw (G_Bw = 0) for each
-    target angle, all targets advanced in lock-step batches (theta decreases
-    as G_Aw becomes more attractive).  Returns (couplings, angles, runs per
-    target)."""
+def bisection(targets_deg, fixed, lo=-0.6, hi=0.3, tol_deg=2.0, max_iter=12, precision="f64", steps=8000,
+              family="A", other=0.0, droplet=None):
+    """Plain lattice-model search: bisection on the varying coupling of a
+    one-parameter family for each target angle, all targets advanced in
+    lock-step batches.  Family "A": G_Aw varies, G_Bw = other (theta falls as
+    G_Aw becomes more attractive); "B": G_Bw varies, G_Aw = other (theta
+    falls as G_Bw becomes more repulsive).  droplet: size keywords of the
+    judging droplets (measure_angles' defaults if None).  Returns
+    (couplings, angles, runs per target)."""
     G, tau_A, tau_B, _ = fixed
     targets = np.asarray(targets_deg, float)
     a = np.full(len(targets), lo)
@@ -183,16 +194,17 @@ def bisection(targets_deg, fixed, lo=-0.6, hi=0.3, tol_deg=2.0, max_iter=12, pre
         if len(idx) == 0:
             break
         mid = 0.5 * (a[idx] + b[idx])
-        ang = measure_angles([(m, 0.0) for m in mid], G, tau_A, tau_B, steps=steps, precision=precision)
+        pairs = [(m, other) if family == "A" else (other, m) for m in mid]
+        ang = measure_angles(pairs, G, tau_A, tau_B, steps=steps, precision=precision, **(droplet or {}))
         runs[idx] += 1
         for j, i in enumerate(idx):
             best[i], best_ang[i] = mid[j], ang[j]
             if abs(ang[j] - targets[i]) <= tol_deg:
                 done[i] = True
-            elif ang[j] > targets[i]:
-                b[i] = mid[j]       # too non-wetting: more attraction (more negative G_Aw)
+            elif (ang[j] > targets[i]) == (family == "A"):
+                b[i] = mid[j]       # A too non-wetting: more attraction (more negative G_Aw)
             else:
-                a[i] = mid[j]
+                a[i] = mid[j]       # B too non-wetting: more repulsion of B (larger G_Bw)
     return best, best_ang, runs
 
 

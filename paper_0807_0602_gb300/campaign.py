@@ -1,6 +1,6 @@
 """Calibration and proposal campaign of the surrogate at the workloads' scale.
 
-    python -m paper_0807_0602_gb300.campaign [--out report.json]
+    python -m paper_0807_0602_gb300.campaign [--out report.json] [--no-calibration]
 
 The paper maps a wall coupling to its contact angle only a posteriori, by
 running the model (Model section, after Eq. 11), and reads capillary filling
@@ -16,21 +16,24 @@ workloads and judges every proposal with the lattice model:
    for 10^4 steps and more (G in [1.0, 1.08], tau = 1): the same droplets
    (256x128, radius 40, 2 10^4 steps) for cos(theta), and capillaries of
    the verification's length (L_cap = 2048, H in [16, 64], 5 10^4 steps) for
-   the Washburn and precursor prefactors;
+   the Washburn and precursor prefactors; the couplings follow the paper's
+   two wetting schemes alone (G_Aw with G_Bw = 0, G_Bw with G_Aw = 0) and
+   combined (G_Aw = -0.5 with G_Bw in [0, 0.6]);
 3. training of the 6 -> 128 -> 128 -> 128 -> 3 network with the device
    kernels (include/mlp.h);
-4. proposals of G_Aw (G_Bw = 0) for 64 target angles 90 j / 63 degrees,
-   j = 0..63, at G = 1.0, tau = 1, H = 64;
+4. proposals for 64 target angles 90 j / 63 degrees, j = 0..63, at G = 1.0,
+   tau = 1, H = 64: along G_Aw in [-0.5, 0.3] (G_Bw = 0) for the angles that
+   family reaches, along G_Bw in [0, 0.6] at G_Aw = -0.5 below them;
 5. verification of every proposal by a 4096x66 capillary (L_cap = 2048,
    H = 64, 5 10^4 FP32 steps): the Washburn prefactor of the front against
    the network's; and by an FP64 sessile droplet (the judge of the angle);
-   targets missed by more than 2 degrees fall back to FP64 bisection near
-   the proposal.
+   reachable targets missed by more than 2 degrees fall back to FP64
+   bisection near the proposal.
 
 The report gives the proposal rate, the angle error of every target, the
 fraction within 2 degrees, the lattice runs used against bisection alone, and
-the range of angles the coupling family reaches (targets outside it cannot be
-met by any coupling of the family and are reported as such).
+the range of angles each coupling family reaches (targets outside them cannot
+be met by any coupling of the families and are reported as such).
 """
 from __future__ import annotations
 
@@ -67,26 +70,43 @@ def capillary_prefactor(run_log, L_cap, mu_l, mu_g, t_min):
     return 2.0 * float(np.polyfit(t[m], F, 1)[0]) / mu_l
 
 
+FAMILIES = {
+    # name: (varying coupling, fixed other coupling, range of the varying one)
+    "A": ("A", 0.0, (-0.5, 0.3)),     # G_Aw varies, G_Bw = 0 (attractive wall for A)
+    "AB": ("B", -0.5, (0.0, 0.6)),    # G_Aw = -0.5 and G_Bw varies (B repelled as well)
+}
+
+
+def pair(family, g):
+    """(G_Aw, G_Bw) of the family member with varying coupling g."""
+    var, other, _ = FAMILIES[family]
+    return (g, other) if var == "A" else (other, g)
+
+
 def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targets=64, H=64, L_cap=2048,
-        cap_steps=50000, train_steps=4000, out=None, log=print):
+        cap_steps=50000, train_steps=4000, out=None, log=print, calibration=True):
     import workloads as W
     from .surrogate import Surrogate
     rep = {}
     t_all = time.perf_counter()
 
     # 1. the calibration batch as specified (G = 1.4)
-    t0 = time.perf_counter()
-    cal = W.batch_sessile_droplets(1024, seed=seed)
-    cpl = [(r["params"]["G_Aw"], r["params"]["G_Bw"]) for r in cal]
-    ang14 = droplet_angles(cpl, 1.4, droplet_steps)
-    rep["calibration_G1.4"] = dict(runs=len(cal), finite=int(np.isfinite(ang14).sum()),
-                                   theta_min=float(np.nanmin(ang14)), theta_max=float(np.nanmax(ang14)),
-                                   seconds=time.perf_counter() - t0)
-    log("calibration G=1.4:", rep["calibration_G1.4"])
+    if calibration:
+        t0 = time.perf_counter()
+        cal = W.batch_sessile_droplets(1024, seed=seed)
+        cpl = [(r["params"]["G_Aw"], r["params"]["G_Bw"]) for r in cal]
+        ang14 = droplet_angles(cpl, 1.4, droplet_steps)
+        rep["calibration_G1.4"] = dict(runs=len(cal), finite=int(np.isfinite(ang14).sum()),
+                                       theta_min=float(np.nanmin(ang14)), theta_max=float(np.nanmax(ang14)),
+                                       seconds=time.perf_counter() - t0)
+        log("calibration G=1.4:", rep["calibration_G1.4"])
 
-    # 2. training set in the stable band
+    # 2. training set in the stable band: the two wetting schemes alone and
+    # combined (G_Aw = -0.5 with a repulsive G_Bw), which reaches the strongly
+    # wetting angles
     t0 = time.perf_counter()
-    X = Cb.sample_parameters(n_train, seed + 100, G=(1.0, 1.08), gA=(-0.5, 0.3), gB=(-0.3, 0.5), H=(16, H))
+    X = Cb.sample_parameters(n_train, seed + 100, G=(1.0, 1.08), gA=(-0.5, 0.3), gB=(-0.3, 0.5), H=(16, H),
+                             both=(-0.5, (0.0, 0.6)))
     ang = np.full(n_train, np.nan)
     runs = [Cb.droplet_run(X[i, 0], X[i, 1], X[i, 2], 1.0, 1.0, **DROP) for i in range(n_train)]
     with Lattice(runs, precision="f32", tile=(128, 16)) as lat:
@@ -103,6 +123,8 @@ def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targ
     ok = np.all(np.isfinite(T), axis=1)
     rep["training_set"] = dict(samples=int(ok.sum()), of=n_train, droplet=dict(DROP, steps=droplet_steps),
                                capillary=dict(L_cap=L_cap, H=[16, H], steps=cap_train_steps),
+                               families={k: dict(varies="G_Aw" if v[0] == "A" else "G_Bw", other=v[1],
+                                                 range=list(v[2])) for k, v in FAMILIES.items()},
                                theta_range=[float(np.nanmin(ang)), float(np.nanmax(ang))],
                                seconds=time.perf_counter() - t0)
     log("training set:", rep["training_set"])
@@ -114,21 +136,34 @@ def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targ
     rep["training"] = dict(steps=train_steps, loss_first=float(losses[:10].mean()),
                            loss_last=float(losses[-50:].mean()), seconds=time.perf_counter() - t0)
 
-    # 4. proposals
+    # 4. the reach of each family (FP64 droplets at its ends), and a family
+    # per target: the wetting scheme alone where it reaches, else the combined one
     targets = np.array([90.0 * j / (n_targets - 1) for j in range(n_targets)])
     fixed = (1.0, 1.0, 1.0, float(H))
+    reach = {}
+    for fam, (_, _, (lo, hi)) in FAMILIES.items():
+        e = droplet_angles([pair(fam, lo), pair(fam, hi)], 1.0, droplet_steps, precision="f64")
+        reach[fam] = (float(np.nanmin(e)), float(np.nanmax(e)))
+    fam_of = np.where(targets >= reach["A"][0], "A", "AB")
+    reachable = np.array([reach[f][0] <= th <= reach[f][1] for f, th in zip(fam_of, targets)])
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prop = sur.propose(np.cos(np.radians(targets)), fixed, family="A", lo=-0.5, hi=0.3)[:, 0]
+    prop = np.zeros((n_targets, 2))
+    for fam in FAMILIES:
+        sel = np.where(fam_of == fam)[0]
+        if len(sel):
+            var, other, (lo, hi) = FAMILIES[fam]
+            prop[sel] = sur.propose(np.cos(np.radians(targets[sel])), fixed, family="A" if var == "A" else "B",
+                                    lo=lo, hi=hi, other=other)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    pred = sur.predict(np.column_stack([prop, np.zeros(n_targets), np.tile(np.array(fixed), (n_targets, 1))]))
+    pred = sur.predict(np.column_stack([prop, np.tile(np.array(fixed), (n_targets, 1))]))
     rep["proposals"] = dict(targets=n_targets, seconds=dt, proposals_per_s=n_targets / dt)
 
     # 5. verification: capillaries (FP32) and droplets (FP64)
     t0 = time.perf_counter()
-    caps = [Cb.capillary_run(L_cap, H, 1.0, 1.0, 1.0, g, 0.0) for g in prop]
+    caps = [Cb.capillary_run(L_cap, H, 1.0, 1.0, 1.0, a, b) for a, b in prop]
     with Lattice(caps, precision="f32", tile=(128, 16), log_every=500, log_capacity=cap_steps // 500 + 2) as lat:
         lat.step(cap_steps)
         logs = [lat.log(i) for i in range(n_targets)]
@@ -137,33 +172,44 @@ def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targ
     rep["capillaries"] = dict(L_cap=L_cap, H=H, grid=[2 * L_cap, H + 2], steps=cap_steps, precision="f32",
                               finite=int(np.isfinite(kw_cap).sum()), seconds=time.perf_counter() - t0)
     t0 = time.perf_counter()
-    ang64 = droplet_angles([(g, 0.0) for g in prop], 1.0, droplet_steps, precision="f64")
+    ang64 = droplet_angles([tuple(p) for p in prop], 1.0, droplet_steps, precision="f64")
     runs_used = np.ones(n_targets, int)
-    # the family's reach at this G: the angles of its end couplings (FP64)
-    reach = droplet_angles([(-0.5, 0.0), (0.3, 0.0)], 1.0, droplet_steps, precision="f64")
-    lo_ang, hi_ang = float(np.nanmin(reach)), float(np.nanmax(reach))
     final = ang64.copy()
-    fallback = np.where((np.abs(ang64 - targets) > 2.0) & (targets >= lo_ang) & (targets <= hi_ang))[0]
-    for i in fallback:
-        c, a2, r = Cb.bisection([targets[i]], fixed, lo=max(-0.5, prop[i] - 0.1), hi=min(0.3, prop[i] + 0.1),
-                                tol_deg=2.0, max_iter=8, precision="f64", steps=droplet_steps)
-        final[i] = a2[0]
-        runs_used[i] += r[0]
-    reachable = (targets >= lo_ang) & (targets <= hi_ang)
-    # the plain lattice search the network replaces: FP64 bisection on G_Aw
-    # over the family's whole range, for the reachable targets
+    miss = (np.abs(ang64 - targets) > 2.0) & reachable
+    for fam in FAMILIES:      # one batched bisection per family near the proposals
+        sel = np.where(miss & (fam_of == fam))[0]
+        if not len(sel):
+            continue
+        var, other, (lo, hi) = FAMILIES[fam]
+        g = prop[sel, 0] if var == "A" else prop[sel, 1]
+        _, a2, r = Cb.bisection(targets[sel], fixed, lo=np.maximum(lo, g - 0.1), hi=np.minimum(hi, g + 0.1),
+                                tol_deg=2.0, max_iter=8, precision="f64", steps=droplet_steps,
+                                family="A" if var == "A" else "B", other=other, droplet=DROP)
+        final[sel] = a2
+        runs_used[sel] += r
+    # the plain lattice search the network replaces: FP64 bisection over each
+    # family's whole range, for the reachable targets
     t1 = time.perf_counter()
-    _, ang_b, runs_b = Cb.bisection(targets[reachable], fixed, lo=-0.5, hi=0.3, tol_deg=2.0, max_iter=12,
-                                    precision="f64", steps=droplet_steps)
-    bis = dict(targets=int(reachable.sum()), lattice_runs=int(runs_b.sum()),
-               within_2deg=float(np.mean(np.abs(ang_b - targets[reachable]) <= 2.0)),
-               seconds=time.perf_counter() - t1)
+    runs_b, hit_b, n_b = 0, 0, 0
+    for fam in FAMILIES:
+        sel = np.where(reachable & (fam_of == fam))[0]
+        if not len(sel):
+            continue
+        var, other, (lo, hi) = FAMILIES[fam]
+        _, ang_b, rb = Cb.bisection(targets[sel], fixed, lo=lo, hi=hi, tol_deg=2.0, max_iter=12, precision="f64",
+                                    steps=droplet_steps, family="A" if var == "A" else "B", other=other,
+                                    droplet=DROP)
+        runs_b += int(rb.sum())
+        hit_b += int(np.sum(np.abs(ang_b - targets[sel]) <= 2.0))
+        n_b += len(sel)
+    bis = dict(targets=n_b, lattice_runs=runs_b, within_2deg=hit_b / max(1, n_b), seconds=time.perf_counter() - t1)
     err_first = np.abs(ang64 - targets)
     err_final = np.abs(final - targets)
     rel_kw = np.abs(kw_cap - pred[:, 1]) / np.abs(kw_cap)
     rep["verification"] = dict(
         judge="FP64 sessile droplets 256x128, radius 40, %d steps" % droplet_steps,
-        family_reach_deg=[lo_ang, hi_ang], reachable_targets=int(reachable.sum()),
+        family_reach_deg={k: list(v) for k, v in reach.items()}, reachable_targets=int(reachable.sum()),
+        targets_per_family={k: int(np.sum(fam_of == k)) for k in FAMILIES},
         within_2deg_first_proposal=float(np.mean(err_first <= 2.0)),
         within_2deg_first_proposal_reachable=float(np.mean(err_first[reachable] <= 2.0)),
         within_2deg_after_fallback_reachable=float(np.mean(err_final[reachable] <= 2.0)),
@@ -174,9 +220,10 @@ def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targ
         washburn_prefactor_rel_err_median=float(np.nanmedian(rel_kw)),
         washburn_prefactor_rel_err_max=float(np.nanmax(rel_kw)),
         seconds=time.perf_counter() - t0,
-        per_target=[dict(theta=float(targets[i]), G_Aw=float(prop[i]), theta_fp64=float(ang64[i]),
-                         theta_final=float(final[i]), runs=int(runs_used[i]),
-                         washburn_capillary=float(kw_cap[i]), washburn_network=float(pred[i, 1]))
+        per_target=[dict(theta=float(targets[i]), family=str(fam_of[i]), G_Aw=float(prop[i, 0]),
+                         G_Bw=float(prop[i, 1]), theta_fp64=float(ang64[i]), theta_final=float(final[i]),
+                         runs=int(runs_used[i]), washburn_capillary=float(kw_cap[i]),
+                         washburn_network=float(pred[i, 1]))
                     for i in range(n_targets)])
     rep["seconds"] = time.perf_counter() - t_all
     if out:
@@ -188,10 +235,11 @@ def run(seed=4, n_train=1024, droplet_steps=20000, cap_train_steps=50000, n_targ
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", default=None)
+    ap.add_argument("--no-calibration", action="store_true", help="skip the 1024-droplet batch at G = 1.4")
     args = ap.parse_args()
     from .build import build
     build()
-    rep = run(out=args.out)
+    rep = run(out=args.out, calibration=not args.no_calibration)
     short = {k: v for k, v in rep.items() if k != "verification"}
     short["verification"] = {k: v for k, v in rep["verification"].items() if k != "per_target"}
     print(json.dumps(short, indent=1))

@@ -178,20 +178,23 @@ class Surrogate:
         return self.tn.inv(y)
 
     def propose(self, targets_cos, fixed, family: str = "A", lo: float = -0.6, hi: float = 0.6,
-                n_cand: int = 1201) -> np.ndarray:
+                n_cand: int = 1201, other: float = 0.0) -> np.ndarray:
         """For each target cos(theta), the coupling on the candidate grid of the
-        one-parameter family (family "A": G_Aw varies, G_Bw = 0; "B": the
+        one-parameter family (family "A": G_Aw varies, G_Bw = other; "B": the
         reverse) whose predicted cos(theta) is closest.  ``fixed`` =
         (G_AB, tau_A, tau_B, H).  Returns [n_targets, 2] couplings (G_Aw, G_Bw)."""
         grid = np.linspace(lo, hi, n_cand)
         X = np.zeros((n_cand, 6))
         if family == "A":
             X[:, 0] = grid
+            X[:, 1] = other
         else:
             X[:, 1] = grid
+            X[:, 0] = other
         X[:, 2:] = np.asarray(fixed, dtype=np.float64)[None, :]
         cos_pred = self.predict(X)[:, 0]
         out = np.zeros((len(targets_cos), 2))
+        out[:, 1 if family == "A" else 0] = other
         for j, c in enumerate(targets_cos):
             k = int(np.argmin(np.abs(cos_pred - c)))
             out[j, 0 if family == "A" else 1] = grid[k]

@@ -96,3 +96,28 @@ def test_coupling_for_angle_inverts_a_table_that_is_bilinear_in_g_and_tau_and_li
         assert abs(got - a) < 1e-12
     assert coupling_for_angle(table, Gs, taus, cps, 1.05, 1.2, 10.0) == -0.5
     assert coupling_for_angle(table, Gs, taus, cps, 1.05, 1.2, 170.0) == 0.3
+
+
+@pytest.mark.parametrize("family,other", [("A", 0.0), ("B", -0.5)])
+def test_bisection_walks_each_coupling_family_the_right_way(monkeypatch, family, other):
+    """The lattice-model bisection on a one-parameter coupling family, with
+    the droplet runs replaced by a monotone angle law (the angle falls as
+    G_Aw falls in family A, and as G_Bw rises in family B at fixed G_Aw):
+    every target inside the family's reach is met within the tolerance and
+    the other coupling stays fixed."""
+    from paper_0807_0602_gb300 import calibrate as Cb
+    seen = []
+
+    def fake(pairs, G, tau_A, tau_B, steps=0, precision="", **kw):
+        seen.extend(pairs)
+        return np.array([80.0 + 60.0 * a - 70.0 * b for a, b in pairs])
+    monkeypatch.setattr(Cb, "measure_angles", fake)
+    lo, hi = (-0.5, 0.3) if family == "A" else (0.0, 0.6)
+    law = (lambda g: 80.0 + 60.0 * g) if family == "A" else (lambda g: 80.0 + 60.0 * other - 70.0 * g)
+    targets = np.array([law(lo) + f * (law(hi) - law(lo)) for f in (0.1, 0.35, 0.6, 0.9)])
+    c, ang, runs = Cb.bisection(targets, (1.0, 1.0, 1.0, 64.0), lo=lo, hi=hi, tol_deg=0.5, max_iter=20,
+                                family=family, other=other)
+    assert np.all(np.abs(ang - targets) <= 0.5)
+    assert np.all((c >= lo) & (c <= hi)) and np.all(runs >= 1)
+    fixed_col = 1 if family == "A" else 0
+    assert all(p[fixed_col] == other for p in seen)
