@@ -59,3 +59,21 @@ def test_bidirectional_march_compiles_for_one_grid(ty, W, gen):
     size = ctypes.c_size_t()
     assert lib.nvrtcGetCUBINSize(prog, ctypes.byref(size)) == 0 and size.value > 1000
     lib.nvrtcDestroyProgram(ctypes.byref(prog))
+
+
+def test_build_embeds_the_headers_verbatim(tmp_path):
+    """The library compiles the grid-specific kernel from header text embedded
+    at build time: write_jit_sources writes each header as one raw string
+    literal, in the order NVRTC is given their names, with the toolkit's
+    include directory."""
+    from paper_0807_0602_gb300 import build as B
+    B.write_jit_sources(str(tmp_path), shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc")
+    text = (tmp_path / "lbm_jit_sources.h").read_text()
+    assert "kJitHeaderCount = 3" in text
+    assert '"lbm.h", "lbm_device.h", "lbm_kernels.cuh"' in text
+    inc = text.split('#define LBM_CUDA_INCLUDE "', 1)[1].split('"', 1)[0]
+    assert os.path.exists(os.path.join(inc, "cuda_fp16.h"))
+    bodies = text.split('R"LBMJIT(')[1:]
+    assert len(bodies) == 3
+    for h, body in zip(HEADERS, bodies):
+        assert body.split(')LBMJIT"', 1)[0] == open(h).read()
